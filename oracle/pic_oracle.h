@@ -1,0 +1,107 @@
+/*
+ * pic_oracle.h -- interface of the plain FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This header, pic_oracle.c and the Python loader
+ * beside them exist to check the CUDA path; only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load them.  The oracle
+ * shares no source with the CUDA library and must never be used as a
+ * fallback for it.
+ *
+ * The oracle follows the paper (arxiv 2609.36383, "An Energy-Conserving
+ * Unstaggered Electromagnetic-Potential PIC Method, Part II") literally:
+ *   - CN potential update and continuity        (Sec. 2.3, Eqs. CN-field, cn-continuity)
+ *   - orbit-averaged shape, deposit, gather    (Sec. 2.4, Eqs. orbit-average-shape .. orbit-gather-general)
+ *   - orbit discrete gradient D_i A            (Sec. 2.5, Eq. D-def)
+ *   - HC magnetic map                          (Sec. 3.2, Defs. hc-normalized, hc-dimensional)
+ *   - GM-HC canonical step                     (Sec. 3.4, Eq. gmhc-step)
+ *   - secant velocity and orbit velocity       (Sec. 4.1-4.2, Eqs. Vdg, vbar-energy)
+ *   - diagnostics                              (Sec. 4.4)
+ *   - Nyquist projector, outer Anderson / inner Picard solve (Sec. 4.5, Algorithm 1)
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAX_SPECIES 4
+
+typedef struct {
+  int dim;            /* active spatial dimensions, 1..3 */
+  int n[3];           /* nodes per dimension (1 for ignorable dims) */
+  double L[3];        /* periodic lengths */
+  double x0[3];       /* position of node 0 */
+  double dt, kappa, sigma1, sigma2;
+  double rho_bg;      /* uniform immobile background charge density */
+  int project;        /* 1: Nyquist projection on (Sec. 4.5) */
+  int gl_points;      /* Gauss-Legendre points per knot-split piece (paper: 8) */
+  int inner_max, outer_max;
+  int anderson_m, anderson_start, backtrack_levels;
+  double beta, lambda, decrease_coef, growth_limit, tol_abs_ratio, inner_tol_scale;
+  int nspecies;
+  double q[ORC_MAX_SPECIES], m[ORC_MAX_SPECIES]; /* per unit weight */
+} orc_params;
+
+typedef struct {
+  double W, K, E_tot, rel_dE;
+  double gauss_rms, lorenz_rms, work_residual, chain_rms;
+  double res_scaled_rms, res_scaled_max;
+  int outer_iters, map_evals, inner_max;
+  double inner_mean;
+  int status;
+} orc_report;
+
+/* status codes (shared meaning with the product ABI, separate definitions) */
+#define ORC_OK 0
+#define ORC_EARG (-1)
+#define ORC_EINNER (-4)
+#define ORC_EOUTER (-5)
+
+void *orc_create(const orc_params *prm);
+void orc_free(void *h);
+int orc_set_particles(void *h, long np, const int *species, const double *x,
+                      const double *u_or_P, int canonical, const double *w);
+int orc_set_potentials(void *h, const double *A, const double *U);
+int orc_start(void *h, orc_report *rep);
+int orc_step(void *h, double tol, orc_report *rep);
+int orc_eval_map(void *h, const double *j, double tol, double *H, double *vbar,
+                 double *Pnew, int *inner_counts);
+long orc_num_particles(void *h);
+int orc_get_particles(void *h, double *x, double *P, double *w, int *species);
+int orc_get_fields(void *h, double *phi, double *psi, double *A, double *U,
+                   double *rho, double *J);
+int orc_set_fields(void *h, const double *phi, const double *psi, const double *A,
+                   const double *U, const double *rho, const double *J);
+
+/* unit-level pieces, exposed so that tests can pin them one by one */
+double orc_S2(double xi);
+double orc_dS2(double xi);
+void orc_gauss_legendre(int n, double *nodes, double *weights);
+void orc_dft(int dim, const int *n, const double *in_re, const double *in_im,
+             double *out_re, double *out_im, int inverse);
+void orc_hc_map(const double *um, const double *B, double qdt_2m, double *up,
+                double *gamma_hc);
+void orc_push(const double *Pn, const double *Am, const double *Ap,
+              const double *gphi, const double *D, const double *vbar, double q,
+              double m, double kappa, double dt, double *pminus, double *pplus,
+              double *Pnp1, double *vnew);
+int orc_orbit_data(void *h, const double *x, const double *vbar,
+                   const double *gradphi, const double *An, const double *Anp1,
+                   const double *Uhalf, double *gphi, double *Ubar, double *D,
+                   double *Aplus, double *Aminus, double *Sbar_sum);
+int orc_field_solve(void *h, const double *j, double *gradphi_half,
+                    double *A_np1, double *U_half, double *phi_np1,
+                    double *psi_np1, double *U_np1, double *rho_np1);
+double orc_field_energy(void *h, const double *phi, const double *A,
+                        const double *U);
+void orc_constraint_rms(void *h, const double *phi, const double *psi,
+                        const double *A, const double *U, const double *rho,
+                        double *gauss_rms, double *lorenz_rms);
+void orc_project(void *h, double *f, int ncomp);
+int orc_deposit(void *h, const double *vbar, double *Jorb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
