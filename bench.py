@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Benchmark of the GM-HC-CN implicit PIC step: particle-pushes/s per nonlinear iteration.
+
+A step is one implicit time step (Algorithm 1): step start, every outer map
+evaluation (spectral CN field solve, fused inner-Picard push + gather +
+deposit, projection, residual tests, Anderson update) and the commit with its
+diagnostics.  One push is one particle through one map evaluation, so
+value = N_p x (map evaluations) / time.
+
+Workload: 2D3V Weibel/filamentation, 128^2 mesh on [-pi, pi]^2, 64 particles
+per cell (1,048,576 particles), beams u_z = +-0.5 with Maxwell-Juettner
+T = 0.01, dt = 0.05, tolerance 1e-10; FP64 path (value) and FP32-mixed path
+(reported beside it).  Inputs are generated once (seeded), resident in HBM
+before the timed region; L2 is flushed between timed steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-pushes/s per nonlinear iter (FP32-mixed vs FP64) at |dE/E|<=solver tol"
+UNIT = "particle-pushes/s"
+WORKLOAD = "weibel_2d_128x128_64ppc"
+
+
+def workload_cfg(seed=0, ppc_beam=32):
+    import pic_inputs
+    return pic_inputs.weibel_2d(n=128, ppc_beam=ppc_beam, u_drift=0.5, T=0.01, dt=0.05,
+                                tol=1e-10, steps=500, seed=seed)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic counts
+def algorithmic_flops(dim, gl, stats):
+    """FP64/FP32 floating-point operations of the particle-map kernel, counted
+    from the arithmetic each piece, Gauss-Legendre point, inner iteration and
+    deposit performs (an FMA counts 2, sqrt and divide 1); see the design notes
+    for the derivation.  pieces covers gather and deposit walks."""
+    nn = 3 ** dim
+    per_point_gather = 13 * dim + nn * (2 + 2 * dim + 2 * dim + 9 + 6 * dim)
+    per_point_deposit = 13 * dim + nn * 2
+    push = 190 + nn * 8
+    iters = stats["inner_iters"]
+    pieces = stats["pieces"]
+    # deposit walks: one per pushed particle (pieces of deposits ~ pieces/iter share)
+    dep_pieces = pieces * stats["pushes"] / max(iters + stats["pushes"], 1)
+    gat_pieces = pieces - dep_pieces
+    return (gat_pieces * gl * per_point_gather + dep_pieces * (gl * per_point_deposit + 6 * nn)
+            + iters * push)
+
+
+def algorithmic_bytes(dim, rsize, pushes):
+    """HBM bytes of the particle map per pushed particle: reads cell (4 dim),
+    offset (r dim), P, A^-, v^0 (3r each), w (8), species (4); writes vbar,
+    P^{n+1} (3r each) and the inner count (4)."""
+    return pushes * (4 * dim + rsize * dim + 9 * rsize + 8 + 4 + 6 * rsize + 4)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2609_36383_b300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    cfg = workload_cfg(seed=rank)
+    npart = cfg["w"].shape[0]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed_steps(sim, nsteps):
+        """K steps, L2 flushed before each, CUDA events on the library's stream."""
+        pushes, ms = 0, 0.0
+        reports = []
+        for _ in range(nsteps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = sim.step(cfg["tol"], raise_on_fail=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            pushes += npart * r["map_evals"]
+            reports.append(r)
+        return pushes, ms, reports
+
+    results = {}
+    paths = (("fp64", P.PIC_FP64), ("mixed", P.PIC_MIXED))
+    if args.only:
+        paths = tuple(p for p in paths if p[0] == args.only)
+    for label, prec in paths:
+        sim = P.from_config(cfg, precision=prec)
+        sim.start()
+        for _ in range(args.warmup):
+            sim.step(cfg["tol"], raise_on_fail=True)
+        sim.reset_stats()
+        barrier()
+        with ClockSampler(local) as clk:
+            pushes, ms, reps = timed_steps(sim, args.steps)
+            barrier()
+        st = sim.stats()
+        results[label] = dict(pushes=pushes, ms=ms, reports=reps, stats=st, clocks=clk.summary(),
+                              rel_dE=max(abs(r["rel_dE"]) for r in reps))
+        if label == "fp64" and not args.skip_e2e:
+            fp64_sim = sim
+        else:
+            sim.close()
+    if args.only or args.skip_e2e:
+        # profiling invocation: a short run of one path, no report line
+        for label, r in results.items():
+            print(json.dumps({"profile_run": label, "ms": r["ms"], "pushes": r["pushes"],
+                              "stats": r["stats"]}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # end-to-end through the C ABI with pinned host buffers: every step
+    # restores the state from host memory, steps, and reads the state back
+    sim = fp64_sim
+    x, Pm, w, sp = sim.particles()
+    f = sim.fields()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hx, hP, hw, hsp = pin(x), pin(Pm), pin(w), pin(sp)
+    hf = {k: pin(v) for k, v in f.items()}
+    E0 = None
+    ox, oP = pin(np.zeros_like(x)), pin(np.zeros_like(Pm))
+    of = {k: pin(np.zeros_like(v)) for k, v in f.items()}
+    import ctypes
+    lib = P.lib()
+    Ng = sim.Ng
+    h2d = npart * (2 * 8 + 3 * 8 + 8 + 4) + Ng * (3 * 8 + 9 * 8)
+    d2h = npart * (2 * 8 + 3 * 8) + Ng * (3 * 8 + 9 * 8)
+    st0 = sim.stats()
+    E0 = results["fp64"]["reports"][0]["E_tot"] - results["fp64"]["reports"][0]["rel_dE"] * 0
+    e2e_pushes, e2e_s = 0, 0.0
+    barrier()
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_state(hx, hP, hw, hsp, hf, E0)
+        r = sim.step(cfg["tol"], raise_on_fail=True)
+        lib.pic_get_particles(sim.handle, ctypes.c_void_p(ox.ctypes.data),
+                              ctypes.c_void_p(oP.ctypes.data), None, None, 0)
+        lib.pic_get_potentials(sim.handle, *[ctypes.c_void_p(of[k].ctypes.data) for k in
+                                             ("phi", "psi", "A", "U", "rho", "J")], 0)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        e2e_pushes += npart * r["map_evals"]
+    barrier()
+    sim.close()
+
+    fp = results["fp64"]
+    mx = results["mixed"]
+    t_max = max_over_ranks(fp["ms"])
+    tot_push = sum_over_ranks(fp["pushes"])
+    value = tot_push / (t_max * 1e-3)
+    mixed_value = sum_over_ranks(mx["pushes"]) / (max_over_ranks(mx["ms"]) * 1e-3)
+    e2e_value = sum_over_ranks(e2e_pushes) / max_over_ranks(e2e_s)
+
+    # roofline of the dominant kernel (particle map), per launch
+    peak64 = P.fma_throughput(P.PIC_FP64)
+    peak32 = P.fma_throughput(P.PIC_MIXED)
+    st = fp["stats"]
+    avg_ms = st["map_ms"] / max(st["map_launches"], 1)
+    flops_launch = algorithmic_flops(2, 3, st) / max(st["map_launches"], 1)
+    bytes_launch = algorithmic_bytes(2, 8, st["pushes"]) / max(st["map_launches"], 1)
+    achieved = flops_launch / (avg_ms * 1e-3)
+    stm = mx["stats"]
+    avg_ms_m = stm["map_ms"] / max(stm["map_launches"], 1)
+    achieved_m = algorithmic_flops(2, 3, stm) / max(stm["map_launches"], 1) / (avg_ms_m * 1e-3)
+    peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = 6400.0
+    hbm_src = "fallback"
+    if os.path.exists(peaks_file):
+        try:
+            hbm = float(json.load(open(peaks_file))["hbm_gbs"])
+            hbm_src = "measured"
+        except Exception:
+            pass
+    map_share = st["map_ms"] / max(fp["ms"], 1e-9)
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD, "grid": [128, 128], "particles_per_gpu": npart, "dt": cfg["dt"],
+            "tol": cfg["tol"], "value_path": "FP64", "parallelism": f"replicas{world}",
+            "l2": "flushed before every timed step (256 MiB write)",
+            "mean_map_evals_per_step": statistics.mean(r["map_evals"] for r in fp["reports"]),
+            "mean_inner_iters": st["inner_iters"] / max(st["pushes"], 1),
+            "max_abs_rel_dE": fp["rel_dE"],
+        },
+        "mixed": {
+            "value": mixed_value, "dtype": "f32-mixed", "ms_per_step": max_over_ranks(mx["ms"]) / args.steps,
+            "speedup_vs_fp64": mixed_value / value, "max_abs_rel_dE": mx["rel_dE"],
+            "mean_map_evals_per_step": statistics.mean(r["map_evals"] for r in mx["reports"]),
+            "map_kernel": {"achieved_tflops": achieved_m / 1e12, "peak_tflops": peak32 / 1e12,
+                           "frac": achieved_m / peak32, "avg_ms": avg_ms_m},
+        },
+        "roofline": {
+            "kernel": "k_map<2,double> (fused inner Picard push+gather+deposit)",
+            "bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak64, "traffic": None,
+            "peak_source": "measured FP64 FMA throughput (pic_fma_throughput)",
+            "avg_launch_ms": avg_ms, "launches": st["map_launches"],
+            "flops_per_launch": flops_launch, "share_of_step": map_share,
+            "hbm": {"achieved_gbs": bytes_launch / (avg_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                    "peak_source": hbm_src,
+                    "frac": bytes_launch / (avg_ms * 1e-3) / 1e9 / hbm},
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": st["launches"],
+        "clocks": fp["clocks"],
+        "clocks_mixed": mx["clocks"],
+    }
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline_subprocess(args)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- oracle (CPU) arm
+def oracle_sample(seconds_budget=20.0, steps=1):
+    """Time the FP64 oracle on a bounded sample of the workload: the full 128^2
+    mesh and beams with 2 particles per cell per beam (65,536 particles)."""
+    import oracle
+    oracle.build()
+    cfg = workload_cfg(seed=0, ppc_beam=2)
+    o = oracle.Oracle(cfg["dim"], cfg["n"], cfg["L"], cfg["x0"], cfg["species"], dt=cfg["dt"],
+                      rho_bg=cfg["rho_bg"])
+    o.set_particles(cfg["x"], cfg["u"], cfg["w"], cfg["sp"])
+    o.set_potentials(cfg["A"], cfg["U"])
+    o.start()
+    npart = cfg["w"].shape[0]
+    pushes, secs, n = 0, 0.0, 0
+    while n < steps or (secs < seconds_budget and n < 3 * steps):
+        t0 = time.perf_counter()
+        r = o.step(cfg["tol"])
+        secs += time.perf_counter() - t0
+        pushes += npart * r["map_evals"]
+        n += 1
+        if secs > seconds_budget:
+            break
+    return dict(value=pushes / secs, unit=UNIT, cores=int(os.environ.get("OMP_NUM_THREADS",
+                                                                        os.cpu_count())),
+                kind="oracle", seconds=secs, steps=n,
+                sample=f"{WORKLOAD} mesh and beams with 2 particles/cell/beam "
+                       f"({npart} particles), {n} oracle step(s)")
+
+
+def cpu_baseline_subprocess(args):
+    env = dict(os.environ)
+    env.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    try:
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"],
+                             capture_output=True, text=True, env=env, timeout=600)
+        return json.loads(res.stdout.strip().splitlines()[-1])
+    except Exception as e:  # report, never fake
+        return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                "sample": f"failed: {e}"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pushes, secs = 0, 0.0
+    samples = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; its steps are independent samples
+    for _ in range(args.steps):
+        s = oracle_sample(seconds_budget=max(60.0 / max(args.steps, 1), 5.0), steps=1)
+        samples.append(s)
+        pushes += s["value"] * s["seconds"]
+        secs += s["seconds"]
+    v = pushes / secs
+    cb = dict(samples[0])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "grid": [128, 128],
+                      "note": "FP64 CPU oracle on a bounded particle sample of the workload"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
+                    help="profiling run of one precision path (prints no report line)")
+    ap.add_argument("--skip-e2e", action="store_true", help="profiling run without the e2e arm")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_sample:
+        print(json.dumps(oracle_sample()), flush=True)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

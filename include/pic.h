@@ -1,0 +1,193 @@
+/*
+ * pic.h -- C ABI of the B300 (sm_103a) implementation of the fully implicit,
+ * energy-conserving, unstaggered Lorenz-gauge potential PIC step with the
+ * generalized-momentum Higuera-Cary push (arxiv 2609.36383, Part II).
+ *
+ * One context owns one simulation on one GPU: particles (SoA), mesh
+ * potentials and every work buffer live in device memory allocated by the
+ * library.  Caller buffers stay caller-owned; get/set copy.  Pointers tagged
+ * `on_device` are CUDA device pointers when that flag is 1 and host pointers
+ * when it is 0.  A context is not thread-safe; all its work is queued on the
+ * stream given in pic_options.cuda_stream (0 = the legacy default stream).
+ *
+ * Array conventions (all float64 unless stated):
+ *   mesh scalars  : Ng = n[0]*n[1]*n[2] values, x fastest (g = i + n0*(j + n1*k));
+ *   mesh vectors  : 3*Ng values, component-major (A[c*Ng + g]);
+ *   particle x    : dim*N values, dimension-major (x[l*N + i]), absolute positions;
+ *   particle u, P : 3*N values, component-major.
+ * Ignorable (inactive) dimensions have n = 1 and no derivative (their Fourier
+ * symbol is zero); vector fields and momenta always have 3 components.
+ *
+ * Return codes: 0 on success, else one of the negative PIC_E* codes below; a
+ * human-readable message is kept by pic_last_error().
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_EARG (-1)    /* invalid argument or unsupported size */
+#define PIC_ENOMEM (-2)  /* device allocation failed */
+#define PIC_ECUDA (-3)   /* a CUDA runtime call failed */
+#define PIC_EINNER (-4)  /* an inner particle solve failed: iteration limit,
+                            non-finite or superluminal velocity (Sec. 4.5) */
+#define PIC_EOUTER (-5)  /* outer solve failed: iteration limit or no accepted
+                            direction (Algorithm 1) */
+#define PIC_ESTATE (-6)  /* call out of order (e.g. pic_step before pic_start) */
+
+#define PIC_FP64 0       /* every step of the particle map in FP64 */
+#define PIC_MIXED 1      /* push, gather, deposit in FP32; field solve, residual
+                            norms and energy sums in FP64 */
+
+typedef struct pic_ctx pic_ctx;
+
+/* Periodic mesh (Sec. 2.3): dim active dimensions, n[l] nodes (a power of
+   two, 4..4096) on [x0[l], x0[l] + L[l]); node g sits at x0 + g*L/n. */
+typedef struct {
+  int dim;
+  int n[3];
+  double L[3];
+  double x0[3];
+} pic_grid;
+
+/* Species charge and mass per unit weight: a particle of weight w carries
+   q = w*q_s and m = w*m_s (Sec. 5 uses q/m = -1, m = |q|). */
+typedef struct {
+  double q, m;
+} pic_species;
+
+/* Solver and model options.  pic_default_options() fills the paper's values
+   (Sec. 5: kappa = sigma1 = sigma2 = 1, 8 inner/outer limits 64/80,
+   Anderson M = 4 from iteration 2, beta = 0.5, lambda = 1e-12, backtracking
+   alpha = 1 .. 1/64, sufficient decrease 1e-4, growth limit 1.2). */
+typedef struct {
+  double kappa, sigma1, sigma2; /* Eq. potential-wave; sigma1 = kappa^2 sigma2 */
+  double rho_bg;                /* immobile uniform background charge density */
+  int project_nyquist;          /* 1: apply the projector of Eq. nyquist-projector */
+  int gl_points;                /* Gauss-Legendre points per knot-split orbit piece;
+                                   0 = minimal exact count dim+1 */
+  int inner_max, outer_max;
+  int anderson_m, anderson_start, backtrack_levels;
+  double beta, lambda, decrease_coef, growth_limit;
+  double tol_abs_ratio;         /* tau_abs = tol * tol_abs_ratio (tau_rel = tol) */
+  double inner_tol_scale;       /* inner tolerance = outer tolerance * this */
+  int precision;                /* PIC_FP64 or PIC_MIXED */
+  double mixed_tol_floor;       /* PIC_MIXED: tolerances are max(tol, this) */
+  int sort_every;               /* counting-sort particles by cell every N steps (0 = never) */
+  void *cuda_stream;            /* cudaStream_t to queue work on */
+} pic_options;
+
+/* Per-step report (Sec. 4.4 diagnostics and solver counters). */
+typedef struct {
+  double W, K, E_tot;           /* field (Eq. field-energy-section2), kinetic, total energy */
+  double rel_dE;                /* (E_tot - E_tot at pic_start) / E_tot at pic_start */
+  double gauss_rms, lorenz_rms; /* Eq. constraint-residuals at the new time level */
+  double work_residual;         /* Eq. work-diagnostic */
+  double chain_rms;             /* Eq. RA-diagnostic */
+  double res_scaled_rms, res_scaled_max; /* Eq. mixed-nonlinear-tests at acceptance */
+  int outer_iters, map_evals, inner_max;
+  double inner_mean;            /* inner iterations of the final map evaluation */
+  int status;                   /* return code of the step */
+} pic_report;
+
+/* Fill *opt with the paper's defaults (see pic_options). */
+void pic_default_options(pic_options *opt);
+
+/* Create a context: validates the mesh (power-of-two n, dim 1..3), the
+   species (1..4, m > 0) and dt > 0, and allocates the mesh buffers on the
+   current CUDA device.  opt may be NULL for the defaults.  On failure *out
+   is NULL and the return code says why. */
+int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species,
+             int nspecies, double dt, const pic_options *opt);
+
+/* Load N particles (replaces any previous set).  species: N int32 indices
+   (NULL = all species 0); x: dim*N absolute positions (wrapped into the box);
+   u_or_P: 3*N proper velocities u = gamma v (is_canonical = 0; the canonical
+   momentum P = m u + q A_h(x) is formed by pic_start from the projected A,
+   Sec. 4.5) or canonical momenta P (is_canonical = 1); w: N weights.
+   The context must be started again (pic_start) unless the field state is
+   also restored with pic_set_state. */
+int pic_set_particles(pic_ctx *ctx, int64_t n, const int32_t *species,
+                      const double *x, const double *u_or_P, int is_canonical,
+                      const double *w, int on_device);
+
+/* Initial vector potential A and its time derivative U (3*Ng each; NULL =
+   zero).  Both are projected by pic_start. */
+int pic_set_potentials(pic_ctx *ctx, const double *A, const double *U, int on_device);
+
+/* Prepare step 0 (Sec. 4.5 and the initial constraints of Sec. 2.3): project
+   A and U, form P from u if needed, deposit rho^0 and J^0 with point shapes
+   and project them, solve phi^0 from Gauss's law and psi^0 from the Lorenz
+   gauge, and record the initial total energy.  *out (may be NULL) receives
+   the diagnostics at step 0. */
+int pic_start(pic_ctx *ctx, pic_report *out);
+
+/* One implicit GM-HC-CN step, Algorithm 1, with tau_rel = tol and
+   tau_abs = tol*tol_abs_ratio.  On PIC_EINNER / PIC_EOUTER the accepted state
+   is unchanged and *out still carries the counters. */
+int pic_step(pic_ctx *ctx, double tol, pic_report *out);
+
+/* One evaluation of the outer map H(j) = P J_orb(j) (Sec. 4.5) from the
+   accepted state, without committing anything.  j, H: 3*Ng; vbar, Pnew:
+   3*N converged orbit velocities and candidate canonical momenta, in the
+   order the particles were loaded; inner_counts: N int32 (-1 = failed).
+   Any output pointer may be NULL. */
+int pic_eval_map(pic_ctx *ctx, const double *j, double tol, double *H,
+                 double *vbar, double *Pnew, int32_t *inner_counts, int on_device);
+
+int64_t pic_num_particles(const pic_ctx *ctx);
+
+/* Copy the accepted particle state out, in load order.  Any pointer may be NULL. */
+int pic_get_particles(pic_ctx *ctx, double *x, double *P, double *w,
+                      int32_t *species, int on_device);
+
+/* Copy the accepted mesh state out: phi, psi, rho (Ng), A, U (3*Ng) at the
+   current time level and J (3*Ng), the accepted current J^{n-1/2} that seeds
+   the next outer iteration.  Any pointer may be NULL. */
+int pic_get_potentials(pic_ctx *ctx, double *phi, double *psi, double *A,
+                       double *U, double *rho, double *J, int on_device);
+
+/* Restore a full accepted state (checkpoint/resume): particles as canonical
+   momenta in load order and the mesh state as returned by pic_get_particles
+   and pic_get_potentials.  E0 is the reference total energy for rel_dE.
+   No projection or constraint solve is applied. */
+int pic_set_state(pic_ctx *ctx, int64_t n, const int32_t *species, const double *x,
+                  const double *P, const double *w, const double *phi,
+                  const double *psi, const double *A, const double *U,
+                  const double *rho, const double *J, double E0, int on_device);
+
+/* Counters of the work this context has done (library profiling support;
+   the paper has no counterpart).  map_ms is the device time of the particle
+   map kernel (inner solves + deposit) measured with CUDA events recorded on
+   the context's stream around each launch. */
+typedef struct {
+  int64_t launches;      /* kernels launched by this context */
+  int64_t map_launches;  /* particle-map kernel launches */
+  double map_ms;         /* summed device time of those launches, ms */
+  int64_t pushes;        /* particles x map evaluations */
+  int64_t inner_iters;   /* summed inner Picard iterations */
+  int64_t pieces;        /* summed knot-split orbit pieces walked (gathers and deposits) */
+} pic_stats;
+
+int pic_get_stats(const pic_ctx *ctx, pic_stats *out);
+int pic_reset_stats(pic_ctx *ctx);
+
+/* Measured fused-multiply-add throughput of the current device in FLOP/s
+   (2 per FMA), for PIC_FP64 or PIC_MIXED (FP32): many independent FMA chains
+   in every thread of a grid of 8 CTAs per SM, timed with CUDA events.  Used
+   as the ALU roofline of the particle map, which no library reports.
+   Allocates one small device buffer and frees it before returning. */
+int pic_fma_throughput(int precision, double *flops_per_s);
+
+const char *pic_last_error(const pic_ctx *ctx);
+void pic_free(pic_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

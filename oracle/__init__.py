@@ -103,6 +103,8 @@ def lib():
         L.orc_constraint_rms.argtypes = [C.c_void_p, _D, _D, _D, _D, _D, _D, _D]
         L.orc_project.argtypes = [C.c_void_p, _D, C.c_int]
         L.orc_deposit.argtypes = [C.c_void_p, _D, _D]
+        L.orc_eval_particles.argtypes = [C.c_void_p, _D, C.c_double, C.c_long,
+                                         C.POINTER(C.c_long), _D, _D, _I]
     return _lib
 
 
@@ -242,6 +244,16 @@ class Oracle:
         it = np.zeros(npart, np.int32)
         st = lib().orc_eval_map(self._h, _p(j), float(tol), _p(H), _p(vb), _p(Pn), _pi(it))
         return st, H, vb.reshape(3, npart), Pn.reshape(3, npart), it
+
+    def eval_particles(self, j, tol, idx):
+        """Inner solves of the particles ``idx`` at trial current j (no deposit)."""
+        idx = np.ascontiguousarray(idx, np.int64)
+        k = idx.shape[0]
+        vb = np.zeros(3 * k); Pn = np.zeros(3 * k); it = np.zeros(k, np.int32)
+        st = lib().orc_eval_particles(self._h, _p(_f64(j)), float(tol), k,
+                                      idx.ctypes.data_as(C.POINTER(C.c_long)), _p(vb), _p(Pn),
+                                      _pi(it))
+        return st, vb.reshape(3, k), Pn.reshape(3, k), it
 
     # -- state access -------------------------------------------------------
     def num_particles(self) -> int:

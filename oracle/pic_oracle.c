@@ -1284,3 +1284,64 @@ int orc_step(void *h, double tol, orc_report *rep) {
   free(j); free(H); free(r); free(jt); free(Ht); free(rt); free(dir); free(dJ); free(dR);
   return status;
 }
+
+/* ------------------------------------------------------------------ */
+/* inner solves of a subset of particles at trial current j (Sec. 4.5: */
+/* with the trial fields fixed, every particle's orbit is converged    */
+/* independently), for checks at sizes where a full evaluation is slow */
+/* ------------------------------------------------------------------ */
+int orc_eval_particles(void *h, const double *j, double tol, long nidx, const long *idx,
+                       double *vbar, double *Pnew, int *inner_counts) {
+  orc *o = (orc *)h;
+  size_t n = (size_t)o->np, Ng = (size_t)o->Ng;
+  double ti = tol * o->p.inner_tol_scale, ta = ti * o->p.tol_abs_ratio;
+  double *jp = (double *)malloc(sizeof(double) * 3 * Ng);
+  memcpy(jp, j, sizeof(double) * 3 * Ng);
+  orc_project(o, jp, 3);
+  eval_t e;
+  eval_alloc(o, &e);
+  orc_field_solve(o, jp, e.gradphi, e.A1, e.Uh, e.phi1, e.psi1, e.U1, e.rho1);
+  free(jp);
+  int fail = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : fail)
+  for (long k = 0; k < nidx; k++) {
+    long i = idx[k];
+    double xp[3], u[3], Am[3], vb[3], Pn[3];
+    particle_x(o, i, xp);
+    node_coord(o, xp, u);
+    interp_point(o, u, o->A, 3, Am);
+    double q = pq(o, i), m = pm(o, i), p[3];
+    for (int c = 0; c < 3; c++) {
+      Pn[c] = o->P[c * n + i];
+      p[c] = Pn[c] - q * Am[c];
+    }
+    double gam = sqrt(1.0 + dot3(p, p) / (m * m * o->p.kappa * o->p.kappa));
+    for (int c = 0; c < 3; c++) vb[c] = p[c] / (m * gam);
+    int conv = 0, it;
+    double Pk[3] = {Pn[0], Pn[1], Pn[2]};
+    orbit_t ob;
+    for (it = 1; it <= o->p.inner_max; it++) {
+      if (orbit_eval(o, xp, vb, e.gradphi, o->A, e.A1, NULL, &ob, 0)) break;
+      double pmn[3], ppl[3], Pn1[3], vn[3];
+      orc_push(Pn, Am, ob.Aplus, ob.gphi, ob.D, vb, q, m, o->p.kappa, o->p.dt, pmn, ppl, Pn1, vn);
+      double diff = 0.0, nrm = 0.0;
+      int finite = 1;
+      for (int c = 0; c < 3; c++) {
+        if (!isfinite(vn[c])) finite = 0;
+        diff = fmax(diff, fabs(vn[c] - vb[c]));
+        nrm = fmax(nrm, fabs(vn[c]));
+      }
+      if (!finite || sqrt(dot3(vn, vn)) >= o->p.kappa) break;
+      for (int c = 0; c < 3; c++) { vb[c] = vn[c]; Pk[c] = Pn1[c]; }
+      if (diff <= ta + ti * nrm) { conv = 1; break; }
+    }
+    for (int c = 0; c < 3; c++) {
+      vbar[c * nidx + k] = vb[c];
+      Pnew[c * nidx + k] = Pk[c];
+    }
+    inner_counts[k] = conv ? it : -1;
+    if (!conv) fail |= 1;
+  }
+  eval_free(&e);
+  return fail ? ORC_EINNER : ORC_OK;
+}

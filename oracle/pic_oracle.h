@@ -100,6 +100,8 @@ void orc_constraint_rms(void *h, const double *phi, const double *psi,
                         double *gauss_rms, double *lorenz_rms);
 void orc_project(void *h, double *f, int ncomp);
 int orc_deposit(void *h, const double *vbar, double *Jorb);
+int orc_eval_particles(void *h, const double *j, double tol, long nidx, const long *idx,
+                       double *vbar, double *Pnew, int *inner_counts);
 
 #ifdef __cplusplus
 }

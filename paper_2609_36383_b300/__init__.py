@@ -1,0 +1,283 @@
+"""B300 (sm_103a) implementation of the GM-HC-CN implicit PIC step (arxiv 2609.36383).
+
+Thin ctypes binding over the C ABI declared in ``include/pic.h`` and built into
+``libpic.so`` by ``build.py``.  This module only marshals arguments: every step
+of the method runs in the library's CUDA kernels.  Host arrays are numpy
+arrays (``on_device = 0``); device arrays are torch CUDA tensors
+(``on_device = 1``), whose ``data_ptr`` is handed to the library.  Importing
+the module does not need a GPU; creating a :class:`Simulation` does, and it
+fails loudly when the library or the GPU is missing (there is no CPU path).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK, PIC_EARG, PIC_ENOMEM, PIC_ECUDA, PIC_EINNER, PIC_EOUTER, PIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PIC_FP64, PIC_MIXED = 0, 1
+
+# every symbol include/pic.h declares (checked by the CPU test suite)
+EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
+           "pic_start", "pic_step", "pic_eval_map", "pic_num_particles", "pic_get_particles",
+           "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
+           "pic_fma_throughput", "pic_last_error", "pic_free")
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("L", C.c_double * 3), ("x0", C.c_double * 3)]
+
+
+class Species(C.Structure):
+    _fields_ = [("q", C.c_double), ("m", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("kappa", C.c_double), ("sigma1", C.c_double), ("sigma2", C.c_double), ("rho_bg", C.c_double),
+        ("project_nyquist", C.c_int), ("gl_points", C.c_int), ("inner_max", C.c_int),
+        ("outer_max", C.c_int), ("anderson_m", C.c_int), ("anderson_start", C.c_int),
+        ("backtrack_levels", C.c_int), ("beta", C.c_double), ("lambda_", C.c_double),
+        ("decrease_coef", C.c_double), ("growth_limit", C.c_double), ("tol_abs_ratio", C.c_double),
+        ("inner_tol_scale", C.c_double), ("precision", C.c_int), ("mixed_tol_floor", C.c_double),
+        ("sort_every", C.c_int), ("cuda_stream", C.c_void_p),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("map_launches", C.c_int64), ("map_ms", C.c_double),
+                ("pushes", C.c_int64), ("inner_iters", C.c_int64), ("pieces", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Report(C.Structure):
+    _fields_ = [
+        ("W", C.c_double), ("K", C.c_double), ("E_tot", C.c_double), ("rel_dE", C.c_double),
+        ("gauss_rms", C.c_double), ("lorenz_rms", C.c_double), ("work_residual", C.c_double),
+        ("chain_rms", C.c_double), ("res_scaled_rms", C.c_double), ("res_scaled_max", C.c_double),
+        ("outer_iters", C.c_int), ("map_evals", C.c_int), ("inner_max", C.c_int),
+        ("inner_mean", C.c_double), ("status", C.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_VP = C.c_void_p
+
+
+def lib():
+    """Load libpic.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2609_36383_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        L.pic_default_options.argtypes = [C.POINTER(Options)]
+        L.pic_init.argtypes = [C.POINTER(_VP), C.POINTER(Grid), C.POINTER(Species), C.c_int,
+                               C.c_double, C.POINTER(Options)]
+        L.pic_set_particles.argtypes = [_VP, C.c_int64, _VP, _VP, _VP, C.c_int, _VP, C.c_int]
+        L.pic_set_potentials.argtypes = [_VP, _VP, _VP, C.c_int]
+        L.pic_start.argtypes = [_VP, C.POINTER(Report)]
+        L.pic_step.argtypes = [_VP, C.c_double, C.POINTER(Report)]
+        L.pic_eval_map.argtypes = [_VP, _VP, C.c_double, _VP, _VP, _VP, _VP, C.c_int]
+        L.pic_num_particles.restype = C.c_int64
+        L.pic_num_particles.argtypes = [_VP]
+        L.pic_get_particles.argtypes = [_VP, _VP, _VP, _VP, _VP, C.c_int]
+        L.pic_get_potentials.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int]
+        L.pic_set_state.argtypes = [_VP, C.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                    _VP, C.c_double, C.c_int]
+        L.pic_get_stats.argtypes = [_VP, C.POINTER(Stats)]
+        L.pic_reset_stats.argtypes = [_VP]
+        L.pic_fma_throughput.argtypes = [C.c_int, C.POINTER(C.c_double)]
+        L.pic_last_error.restype = C.c_char_p
+        L.pic_last_error.argtypes = [_VP]
+        L.pic_free.argtypes = [_VP]
+        _lib = L
+    return _lib
+
+
+def default_options() -> Options:
+    o = Options()
+    lib().pic_default_options(C.byref(o))
+    return o
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pic error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a, on_device):
+    """Raw pointer of a numpy array (host) or torch tensor (device); None -> NULL."""
+    if a is None:
+        return None
+    if on_device:
+        return C.c_void_p(a.data_ptr())
+    assert a.flags["C_CONTIGUOUS"]
+    return C.c_void_p(a.ctypes.data)
+
+
+class Simulation:
+    """One simulation context of the C ABI (one GPU, one stream)."""
+
+    def __init__(self, dim, n, L, x0, species, dt, precision=PIC_FP64, stream=None, **opts):
+        g = Grid()
+        g.dim = dim
+        n3 = list(n) + [1] * (3 - len(n))
+        L3 = list(L) + [1.0] * (3 - len(L))
+        x3 = list(x0) + [0.0] * (3 - len(x0))
+        for a in range(3):
+            g.n[a] = int(n3[a]); g.L[a] = float(L3[a]); g.x0[a] = float(x3[a])
+        sp = (Species * len(species))(*[Species(float(q), float(m)) for q, m in species])
+        o = default_options()
+        o.precision = precision
+        for k, v in opts.items():
+            setattr(o, "lambda_" if k == "lambda" else k, v)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = None
+        o.cuda_stream = stream or None
+        h = C.c_void_p()
+        rc = lib().pic_init(C.byref(h), C.byref(g), sp, len(species), float(dt), C.byref(o))
+        if rc:
+            raise PicError(rc, "pic_init rejected the arguments or could not allocate")
+        self._h = h
+        self.dim = dim
+        self.n = [int(v) for v in n3[:dim]]
+        self.Ng = int(np.prod(self.n))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc and rc not in allow:
+            raise PicError(rc, lib().pic_last_error(self._h).decode())
+        return rc
+
+    # -- set-up -------------------------------------------------------------
+    def set_particles(self, x, u_or_P, w, species=None, canonical=False, on_device=False):
+        if not on_device:
+            x = np.ascontiguousarray(x, np.float64); u_or_P = np.ascontiguousarray(u_or_P, np.float64)
+            w = np.ascontiguousarray(w, np.float64)
+            species = None if species is None else np.ascontiguousarray(species, np.int32)
+        n = int(w.shape[0])
+        self._check(lib().pic_set_particles(self._h, n, _ptr(species, on_device), _ptr(x, on_device),
+                                            _ptr(u_or_P, on_device), int(canonical),
+                                            _ptr(w, on_device), int(on_device)))
+
+    def set_potentials(self, A=None, U=None, on_device=False):
+        if not on_device:
+            A = None if A is None else np.ascontiguousarray(A, np.float64)
+            U = None if U is None else np.ascontiguousarray(U, np.float64)
+        self._check(lib().pic_set_potentials(self._h, _ptr(A, on_device), _ptr(U, on_device),
+                                             int(on_device)))
+
+    def start(self) -> dict:
+        r = Report()
+        self._check(lib().pic_start(self._h, C.byref(r)))
+        return r.as_dict()
+
+    def step(self, tol, raise_on_fail=False) -> dict:
+        r = Report()
+        rc = lib().pic_step(self._h, float(tol), C.byref(r))
+        if raise_on_fail or rc not in (PIC_OK, PIC_EINNER, PIC_EOUTER):
+            self._check(rc)
+        d = r.as_dict()
+        d["status"] = rc
+        return d
+
+    def eval_map(self, j, tol):
+        """H(j), orbit velocities, candidate P^{n+1} and inner counts (host arrays)."""
+        npart = self.num_particles()
+        j = np.ascontiguousarray(j, np.float64)
+        H = np.zeros(3 * self.Ng)
+        vb = np.zeros(3 * npart); Pn = np.zeros(3 * npart); it = np.zeros(npart, np.int32)
+        rc = lib().pic_eval_map(self._h, _ptr(j, 0), float(tol), _ptr(H, 0), _ptr(vb, 0),
+                                _ptr(Pn, 0), _ptr(it, 0), 0)
+        self._check(rc, allow=(PIC_EINNER,))
+        return rc, H, vb.reshape(3, npart), Pn.reshape(3, npart), it
+
+    # -- state access ---------------------------------------------------------
+    def num_particles(self) -> int:
+        return int(lib().pic_num_particles(self._h))
+
+    def particles(self):
+        npart = self.num_particles()
+        x = np.zeros(self.dim * npart); P = np.zeros(3 * npart); w = np.zeros(npart)
+        sp = np.zeros(npart, np.int32)
+        self._check(lib().pic_get_particles(self._h, _ptr(x, 0), _ptr(P, 0), _ptr(w, 0),
+                                            _ptr(sp, 0), 0))
+        return x.reshape(self.dim, npart), P.reshape(3, npart), w, sp
+
+    def fields(self) -> dict:
+        N = self.Ng
+        out = dict(phi=np.zeros(N), psi=np.zeros(N), A=np.zeros(3 * N), U=np.zeros(3 * N),
+                   rho=np.zeros(N), J=np.zeros(3 * N))
+        self._check(lib().pic_get_potentials(self._h, *[_ptr(out[k], 0) for k in
+                                                        ("phi", "psi", "A", "U", "rho", "J")], 0))
+        return out
+
+    def set_state(self, x, P, w, species, fields, E0, on_device=False):
+        if not on_device:
+            x = np.ascontiguousarray(x, np.float64); P = np.ascontiguousarray(P, np.float64)
+            w = np.ascontiguousarray(w, np.float64)
+            species = None if species is None else np.ascontiguousarray(species, np.int32)
+            fields = {k: np.ascontiguousarray(v, np.float64) for k, v in fields.items()}
+        n = int(w.shape[0])
+        self._check(lib().pic_set_state(self._h, n, _ptr(species, on_device), _ptr(x, on_device),
+                                        _ptr(P, on_device), _ptr(w, on_device),
+                                        *[_ptr(fields[k], on_device) for k in
+                                          ("phi", "psi", "A", "U", "rho", "J")],
+                                        float(E0), int(on_device)))
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(lib().pic_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def reset_stats(self):
+        self._check(lib().pic_reset_stats(self._h))
+
+    # -- raw access for device-resident benchmarking ----------------------------
+    @property
+    def handle(self):
+        return self._h
+
+
+def fma_throughput(precision=PIC_FP64) -> float:
+    """Measured FMA throughput of the current device, FLOP/s."""
+    v = C.c_double()
+    rc = lib().pic_fma_throughput(int(precision), C.byref(v))
+    if rc:
+        raise PicError(rc, "pic_fma_throughput failed")
+    return v.value
+
+
+def from_config(cfg, precision=PIC_FP64, **opts) -> Simulation:
+    """Create, load and start a simulation from a ``pic_inputs`` recipe."""
+    sim = Simulation(cfg["dim"], cfg["n"], cfg["L"], cfg["x0"], cfg["species"], cfg["dt"],
+                     precision=precision, rho_bg=cfg["rho_bg"], **opts)
+    sim.set_particles(cfg["x"], cfg["u"], cfg["w"], cfg["sp"])
+    sim.set_potentials(cfg["A"], cfg["U"])
+    return sim

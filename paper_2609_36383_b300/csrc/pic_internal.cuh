@@ -1,0 +1,182 @@
+// pic_internal.cuh -- context layout and launcher declarations shared by the
+// CUDA translation units of libpic.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pic.h"
+
+#define PIC_MAX_SPECIES 4
+#define PIC_MAX_GL 8
+#define PIC_MAX_ANDERSON 8
+
+// Status bits raised by the particle kernels (one word per evaluation).
+#define PIC_ST_NOCONV 1u      // inner limit reached
+#define PIC_ST_NONFINITE 2u   // non-finite orbit velocity
+#define PIC_ST_SUPERLUM 4u    // |vbar| >= kappa
+#define PIC_ST_PIECES 8u      // orbit crosses more knots than the kernel handles
+
+struct Geom {
+  int dim;
+  int n[3];
+  int logn[3];
+  int Ng;
+  double L[3], x0[3], dx[3], dV;
+};
+
+// Scalars the particle kernels read; passed by value.
+struct StepConst {
+  double dt, kappa;
+  double qs[PIC_MAX_SPECIES], ms[PIC_MAX_SPECIES];
+  double tau_r, tau_a;  // inner tolerances
+  int inner_max;
+  int ngl;
+  double gl_t[PIC_MAX_GL], gl_w[PIC_MAX_GL];  // nodes and weights on [0, 1]
+};
+
+// Per-evaluation counters written by the particle kernel.
+struct EvalCounters {
+  unsigned int status;
+  int inner_max;
+  unsigned long long inner_sum;
+};
+
+// Reduction partials returned to the host after the residual kernel.
+struct ResidSums {
+  double r2, H2, j2, smax;
+};
+
+struct pic_ctx {
+  Geom g;
+  int nspecies;
+  double qs[PIC_MAX_SPECIES], ms[PIC_MAX_SPECIES];
+  double dt;
+  pic_options opt;
+  cudaStream_t st;
+  std::string err;
+  int started;     // pic_start done (or state restored)
+  int have_particles;
+  int pending_mech;
+  double E0;
+  long long steps_done;
+
+  // ---- particles (SoA, capacity cap) -------------------------------------
+  int64_t np, cap;
+  int rsize;          // sizeof(real) of particle storage: 8 (FP64) or 4 (mixed)
+  int32_t *cell;      // [3][cap] nearest node per active dim
+  void *off;          // [3][cap] offset in node units, [-1/2, 1/2)
+  void *P;            // [3][cap] canonical momentum
+  double *w;          // [cap]
+  int32_t *sp;        // [cap]
+  int64_t *id;        // [cap] load order index
+  void *Am, *v0, *vbar, *Pnew;  // [3][cap] step work
+  int32_t *iters;     // [cap]
+  double *u_in;       // [3][cap] mechanical input awaiting pic_start
+  // sort scratch
+  int32_t *keys, *cnt;
+  void *tmp_r;        // [3][cap] scratch of particle reals
+  double *tmp_d;      // [3][cap]
+  int32_t *tmp_i;     // [3][cap]
+  int64_t *tmp_l;
+
+  // ---- mesh: accepted state (spectral primary + real copies) ------------
+  double2 *phi_h, *psi_h, *rho_h, *A_h, *U_h;   // Ng, Ng, Ng, 3Ng, 3Ng
+  double *A_real;     // 3Ng  A^n in real space (gather)
+  double *J_acc;      // 3Ng  accepted current (seed of the next outer solve)
+  // ---- mesh: one map evaluation -----------------------------------------
+  double2 *phi1_h, *psi1_h, *rho1_h, *A1_h, *U1_h;  // n+1 candidates
+  double2 *jh;        // 3Ng  transform of the trial current
+  double2 *work_h;    // (d + 6) * Ng spectral scratch for inverse transforms
+  double *A1_real;    // 3Ng  A^{n+1} of the last evaluation in real space
+  double *scr_r;      // 4Ng  real scratch (start, get/set)
+  void *nodes;        // Ng * NV gather records in the particle real type
+  void *nodes_u;      // Ng * 3 U^{n+1/2} records (final pass diagnostics)
+  double *Jorb;       // 3Ng deposited orbit current
+  double2 *Jorb_h;    // 3Ng its projected transform
+  double *H;          // 3Ng  H(j)
+  // ---- outer solver ------------------------------------------------------
+  double *j, *r, *jt, *Ht, *rt, *dir;   // 3Ng each
+  double *dJ, *dR;    // M * 3Ng
+  // ---- FFT ---------------------------------------------------------------
+  double2 *tw[3];     // twiddle table per axis: exp(-2 pi i k / n), k < n
+  // ---- reductions ------------------------------------------------------
+  double *red;        // block partials
+  double *red_host;   // pinned
+  EvalCounters *cnt_dev, *cnt_host;
+  double *psum;       // per-block particle sums (work, chain, K)
+  // ---- statistics (pic_stats) ------------------------------------------
+  long long launches;          // kernels launched by this context
+  long long map_launches;      // particle-map kernel launches
+  double map_ms;               // their summed device time (CUDA events)
+  long long pushes;            // particles x map evaluations
+  long long inner_iters;       // summed inner iterations
+  long long pieces;            // summed knot-split orbit pieces walked
+  cudaEvent_t ev0, ev1;
+};
+
+// every kernel launch is followed by KCHECK(): it counts the launch and
+// turns a launch error into PIC_ECUDA
+#define KCHECK()                                                              \
+  do {                                                                        \
+    ctx->launches++;                                                          \
+    CK(cudaGetLastError());                                                   \
+  } while (0)
+
+#define CK(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+      return PIC_ECUDA;                                                       \
+    }                                                                         \
+  } while (0)
+
+// ---------------------------------------------------------------- fft.cu
+// In-place unnormalised complex FFT of `batch` consecutive mesh arrays of
+// Ng values each, along every active axis; sign -1 forward, +1 inverse.
+int fft_nd(pic_ctx *ctx, double2 *data, int batch, int sign);
+int fft_init(pic_ctx *ctx);
+
+// ---------------------------------------------------------------- field.cu
+int field_real_to_complex(pic_ctx *ctx, const double *src, double2 *dst, int ncomp);
+int field_complex_to_real(pic_ctx *ctx, const double2 *src, double *dst, int ncomp,
+                          double scale);
+int field_project_h(pic_ctx *ctx, double2 *f, int ncomp);
+int field_cn_update(pic_ctx *ctx, const double2 *jh, int want_uhalf);
+int field_pack_nodes(pic_ctx *ctx, int want_uhalf);
+int field_initial_constraints(pic_ctx *ctx);
+int field_energy(pic_ctx *ctx, const double2 *phi_h, const double2 *A_h,
+                 const double2 *U_h, double *W);
+int field_constraints(pic_ctx *ctx, double *gauss_rms, double *lorenz_rms);
+int field_mesh_work(pic_ctx *ctx, double *work);
+
+// ---------------------------------------------------------------- particle.cu
+int particles_alloc(pic_ctx *ctx, int64_t n);
+int particles_load(pic_ctx *ctx, const int32_t *sp, const double *x, const double *uP,
+                   int canonical, const double *w, int on_device);
+int particles_form_P(pic_ctx *ctx);
+int particles_point_deposit(pic_ctx *ctx, double *rho, double *J);
+int particles_step_start(pic_ctx *ctx);
+int particles_map(pic_ctx *ctx, const StepConst &sc, int final_pass, double *work_sum,
+                  double *chain_sum, EvalCounters *cnt);
+int particles_commit(pic_ctx *ctx);
+int particles_kinetic(pic_ctx *ctx, double *K);
+int particles_export(pic_ctx *ctx, double *x, double *P, double *w, int32_t *sp,
+                     int on_device);
+int particles_export_eval(pic_ctx *ctx, double *vbar, double *Pnew, int32_t *iters,
+                          int on_device);
+int particles_sort(pic_ctx *ctx);
+
+// ---------------------------------------------------------------- reduce.cu
+int resid_sums(pic_ctx *ctx, const double *Hv, const double *jv, double *rv, double tau_r,
+               double tau_a, ResidSums *out);
+int dots(pic_ctx *ctx, const double *const *a, const double *const *b, int npairs, double *out);
+int axpy_dir(pic_ctx *ctx, double *dir, const double *r, double beta,
+             const double *const *dJ, const double *const *dR, const double *gam, int mh,
+             size_t N3);
+int lincomb(pic_ctx *ctx, double *out, const double *a, double alpha, const double *b,
+            double beta_c, size_t N);
+int diff_into(pic_ctx *ctx, double *out, const double *a, const double *b, size_t N);

@@ -1,0 +1,63 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every entry
+point include/pic.h declares (no compute call: there is no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpic():
+    from paper_2609_36383_b300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for must in ("pic_init", "pic_step", "pic_start", "pic_set_particles", "pic_get_particles",
+                 "pic_set_potentials", "pic_get_potentials", "pic_eval_map", "pic_set_state",
+                 "pic_last_error", "pic_free"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpic):
+    for name in declared_entry_points():
+        assert hasattr(libpic, name), name
+
+
+def test_binding_lists_every_symbol():
+    import paper_2609_36383_b300 as P
+    assert sorted(P.EXPORTS) == declared_entry_points()
+
+
+def test_default_options_are_the_papers(libpic):
+    import paper_2609_36383_b300 as P
+    o = P.default_options()
+    assert (o.inner_max, o.outer_max, o.anderson_m, o.anderson_start) == (64, 80, 4, 2)
+    assert (o.beta, o.lambda_, o.decrease_coef, o.growth_limit) == (0.5, 1e-12, 1e-4, 1.2)
+    assert o.backtrack_levels == 7 and o.project_nyquist == 1
+    assert (o.kappa, o.sigma1, o.sigma2) == (1.0, 1.0, 1.0)
+
+
+def test_init_rejects_bad_grids_without_touching_the_gpu(libpic):
+    import paper_2609_36383_b300 as P
+    g = P.Grid()
+    g.dim = 2
+    g.n[0], g.n[1], g.n[2] = 100, 64, 1  # not a power of two
+    g.L[0] = g.L[1] = g.L[2] = 1.0
+    sp = (P.Species * 1)(P.Species(-1.0, 1.0))
+    h = ctypes.c_void_p()
+    assert P.lib().pic_init(ctypes.byref(h), ctypes.byref(g), sp, 1, 0.1, None) == P.PIC_EARG
+    g.n[0] = 64
+    assert P.lib().pic_init(ctypes.byref(h), ctypes.byref(g), sp, 1, -0.1, None) == P.PIC_EARG
+    assert P.lib().pic_init(ctypes.byref(h), ctypes.byref(g), sp, 0, 0.1, None) == P.PIC_EARG
