@@ -39,6 +39,8 @@ extern "C" {
 #define PIC_EOUTER (-5)  /* outer solve failed: iteration limit or no accepted
                             direction (Algorithm 1) */
 #define PIC_ESTATE (-6)  /* call out of order (e.g. pic_step before pic_start) */
+#define PIC_ETOOBIG (-7) /* input larger than a fixed-size buffer allows
+                            (pic_kinetic_energy_noalloc) */
 
 #define PIC_FP64 0       /* every step of the particle map in FP64 */
 #define PIC_MIXED 1      /* push, gather, deposit in FP32; field solve, residual
@@ -183,6 +185,35 @@ int pic_reset_stats(pic_ctx *ctx);
    as the ALU roofline of the particle map, which no library reports.
    Allocates one small device buffer and frees it before returning. */
 int pic_fma_throughput(int precision, double *flops_per_s);
+
+/* Kinetic energy sum_i m_i kappa^2 (gamma_i - 1), with p_i = P_i - q_i A_h(x_i),
+   of a particle set in a mesh vector potential, computed WITHOUT ALLOCATING
+   ANY MEMORY.  The paper has no counterpart: this entry point serves callers
+   that cannot call cudaMalloc, for example code whose memory pool or arena
+   owns the whole device, code inside a latency-critical loop where an
+   allocation would synchronize the device, or frameworks that forbid
+   allocations on their hot path.  It computes the same sum that pic_start
+   and pic_step report as K, but needs no context.
+   Arguments: grid, species (1..4) and kappa as for pic_init; n particles
+   with DEVICE arrays sp (n int32, NULL = species 0), x (dim*n absolute
+   positions), P (3*n canonical momenta), w (n weights), A (3*Ng vector
+   potential, layout as in pic_get_potentials); *K_out is a HOST double.
+   All work is queued on cuda_stream (NULL = legacy default stream) and the
+   call returns after that stream has finished it.
+   Scratch: a fixed 128 KiB array of device memory inside the library, which
+   every GPU that loads the library holds until the process exits; at most
+   PIC_NOALLOC_MAX_PARTICLES particles, larger n returns PIC_ETOOBIG.  The
+   first call on each device looks up that array's device address
+   (cudaGetSymbolAddress) with the device current; make that first call
+   before any stream capture.  Every call shares the array, so calls whose
+   work overlaps on the GPU (other streams, other threads) race and must be
+   serialised by the caller.  Returns PIC_EARG on invalid arguments and
+   PIC_ECUDA if a launch or copy fails. */
+#define PIC_NOALLOC_MAX_PARTICLES (16384LL * 256LL)
+int pic_kinetic_energy_noalloc(const pic_grid *grid, const pic_species *species, int nspecies,
+                               double kappa, int64_t n, const int32_t *sp, const double *x,
+                               const double *P, const double *w, const double *A,
+                               double *K_out, void *cuda_stream);
 
 const char *pic_last_error(const pic_ctx *ctx);
 void pic_free(pic_ctx *ctx);

@@ -19,13 +19,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpic.so")
 
 PIC_OK, PIC_EARG, PIC_ENOMEM, PIC_ECUDA, PIC_EINNER, PIC_EOUTER, PIC_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PIC_ETOOBIG = -7
+NOALLOC_MAX_PARTICLES = 16384 * 256
 PIC_FP64, PIC_MIXED = 0, 1
 
 # every symbol include/pic.h declares (checked by the CPU test suite)
 EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
            "pic_start", "pic_step", "pic_eval_map", "pic_num_particles", "pic_get_particles",
            "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
-           "pic_fma_throughput", "pic_last_error", "pic_free")
+           "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free")
 
 
 class Grid(C.Structure):
@@ -97,6 +99,9 @@ def lib():
         L.pic_get_stats.argtypes = [_VP, C.POINTER(Stats)]
         L.pic_reset_stats.argtypes = [_VP]
         L.pic_fma_throughput.argtypes = [C.c_int, C.POINTER(C.c_double)]
+        L.pic_kinetic_energy_noalloc.argtypes = [C.POINTER(Grid), C.POINTER(Species), C.c_int,
+                                                 C.c_double, C.c_int64, _VP, _VP, _VP, _VP, _VP,
+                                                 C.POINTER(C.c_double), _VP]
         L.pic_last_error.restype = C.c_char_p
         L.pic_last_error.argtypes = [_VP]
         L.pic_free.argtypes = [_VP]
