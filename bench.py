@@ -100,22 +100,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- algorithmic counts
-def algorithmic_flops(dim, gl, stats):
-    """FP64/FP32 floating-point operations of the particle-map kernel, counted
-    from the arithmetic each piece, Gauss-Legendre point, inner iteration and
-    deposit performs (an FMA counts 2, sqrt and divide 1); see the design notes
-    for the derivation.  pieces covers gather and deposit walks."""
-    nn = 3 ** dim
-    per_point_gather = 13 * dim + nn * (2 + 2 * dim + 2 * dim + 9 + 6 * dim)
-    per_point_deposit = 13 * dim + nn * 2
-    push = 190 + nn * 8
-    iters = stats["inner_iters"]
-    pieces = stats["pieces"]
-    # deposit walks: one per pushed particle (pieces of deposits ~ pieces/iter share)
-    dep_pieces = pieces * stats["pushes"] / max(iters + stats["pushes"], 1)
+# Floating-point operations of the particle map, counted from the arithmetic
+# the method needs (an FMA counts 2, a sqrt or divide 1), with the minimal
+# exact Gauss-Legendre rule (dim + 1 points per knot-split piece):
+#   GATHER_PIECE: weights of the 3^dim nodes accumulated over the points of
+#                 one piece (S, dS/du, s dS/du) and one contraction with the
+#                 node records (grad phi-bar and the 3 x dim discrete gradient);
+#   ITER:         A+ interpolation, GM-HC push, secant orbit velocity, test;
+#   DEPOSIT_PIECE: orbit weights of one piece and the 3 x 3^dim deposit values.
+GATHER_PIECE = {1: 2 * 33 + 51, 2: 3 * 129 + 279, 3: 4 * 471 + 1215}
+ITER = {1: 195, 2: 258, 3: 405}
+DEPOSIT_PIECE = {1: 45, 2: 153, 3: 453}
+
+
+def algorithmic_flops(dim, stats):
+    """Flops of the particle-map launches summarised by pic_get_stats: every
+    inner iteration walks its orbit's pieces (gather) and every pushed
+    particle walks its final orbit once more (deposit); stats['pieces']
+    counts both walks, split here in proportion to the number of walks."""
+    iters, pushes, pieces = stats["inner_iters"], stats["pushes"], stats["pieces"]
+    dep_pieces = pieces * pushes / max(iters + pushes, 1)
     gat_pieces = pieces - dep_pieces
-    return (gat_pieces * gl * per_point_gather + dep_pieces * (gl * per_point_deposit + 6 * nn)
-            + iters * push)
+    return gat_pieces * GATHER_PIECE[dim] + iters * ITER[dim] + dep_pieces * DEPOSIT_PIECE[dim]
 
 
 def algorithmic_bytes(dim, rsize, pushes):
@@ -123,6 +129,20 @@ def algorithmic_bytes(dim, rsize, pushes):
     offset (r dim), P, A^-, v^0 (3r each), w (8), species (4); writes vbar,
     P^{n+1} (3r each) and the inner count (4)."""
     return pushes * (4 * dim + rsize * dim + 9 * rsize + 8 + 4 + 6 * rsize + 4)
+
+
+# ---------------------------------------------------------------- rank aggregation
+def aggregate(dist, pushes, ms, device="cpu"):
+    """Whole-job throughput of N independent replicas: the units every rank
+    processed over the slowest rank's time (max over ranks)."""
+    import torch
+    if dist is None:
+        return pushes / (ms * 1e-3), ms
+    t = torch.tensor([float(pushes)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(t.item()) / (float(m.item()) * 1e-3), float(m.item())
 
 
 # ---------------------------------------------------------------- our arm
@@ -146,20 +166,6 @@ def run_ours(args):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
 
     cfg = workload_cfg(seed=rank)
     npart = cfg["w"].shape[0]
@@ -187,6 +193,9 @@ def run_ours(args):
     paths = (("fp64", P.PIC_FP64), ("mixed", P.PIC_MIXED))
     if args.only:
         paths = tuple(p for p in paths if p[0] == args.only)
+    # one clock sampler spans both timed regions (the mixed one alone is far
+    # shorter than nvidia-smi's sampling interval)
+    clk = ClockSampler(local).__enter__()
     for label, prec in paths:
         sim = P.from_config(cfg, precision=prec)
         sim.start()
@@ -194,16 +203,17 @@ def run_ours(args):
             sim.step(cfg["tol"], raise_on_fail=True)
         sim.reset_stats()
         barrier()
-        with ClockSampler(local) as clk:
-            pushes, ms, reps = timed_steps(sim, args.steps)
-            barrier()
+        pushes, ms, reps = timed_steps(sim, args.steps)
+        barrier()
         st = sim.stats()
-        results[label] = dict(pushes=pushes, ms=ms, reports=reps, stats=st, clocks=clk.summary(),
+        results[label] = dict(pushes=pushes, ms=ms, reports=reps, stats=st,
                               rel_dE=max(abs(r["rel_dE"]) for r in reps))
         if label == "fp64" and not args.skip_e2e:
             fp64_sim = sim
         else:
             sim.close()
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
     if args.only or args.skip_e2e:
         # profiling invocation: a short run of one path, no report line
         for label, r in results.items():
@@ -250,23 +260,21 @@ def run_ours(args):
 
     fp = results["fp64"]
     mx = results["mixed"]
-    t_max = max_over_ranks(fp["ms"])
-    tot_push = sum_over_ranks(fp["pushes"])
-    value = tot_push / (t_max * 1e-3)
-    mixed_value = sum_over_ranks(mx["pushes"]) / (max_over_ranks(mx["ms"]) * 1e-3)
-    e2e_value = sum_over_ranks(e2e_pushes) / max_over_ranks(e2e_s)
+    value, t_max = aggregate(dist, fp["pushes"], fp["ms"], "cuda")
+    mixed_value, mx_ms = aggregate(dist, mx["pushes"], mx["ms"], "cuda")
+    e2e_value, _ = aggregate(dist, e2e_pushes, e2e_s * 1e3, "cuda")
 
     # roofline of the dominant kernel (particle map), per launch
     peak64 = P.fma_throughput(P.PIC_FP64)
     peak32 = P.fma_throughput(P.PIC_MIXED)
     st = fp["stats"]
     avg_ms = st["map_ms"] / max(st["map_launches"], 1)
-    flops_launch = algorithmic_flops(2, 3, st) / max(st["map_launches"], 1)
+    flops_launch = algorithmic_flops(2, st) / max(st["map_launches"], 1)
     bytes_launch = algorithmic_bytes(2, 8, st["pushes"]) / max(st["map_launches"], 1)
     achieved = flops_launch / (avg_ms * 1e-3)
     stm = mx["stats"]
     avg_ms_m = stm["map_ms"] / max(stm["map_launches"], 1)
-    achieved_m = algorithmic_flops(2, 3, stm) / max(stm["map_launches"], 1) / (avg_ms_m * 1e-3)
+    achieved_m = algorithmic_flops(2, stm) / max(stm["map_launches"], 1) / (avg_ms_m * 1e-3)
     peaks_file = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm = 6400.0
     hbm_src = "fallback"
@@ -300,7 +308,7 @@ def run_ours(args):
             "max_abs_rel_dE": fp["rel_dE"],
         },
         "mixed": {
-            "value": mixed_value, "dtype": "f32-mixed", "ms_per_step": max_over_ranks(mx["ms"]) / args.steps,
+            "value": mixed_value, "dtype": "f32-mixed", "ms_per_step": mx_ms / args.steps,
             "speedup_vs_fp64": mixed_value / value, "max_abs_rel_dE": mx["rel_dE"],
             "mean_map_evals_per_step": statistics.mean(r["map_evals"] for r in mx["reports"]),
             "map_kernel": {"achieved_tflops": achieved_m / 1e12, "peak_tflops": peak32 / 1e12,
@@ -320,8 +328,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": st["launches"],
-        "clocks": fp["clocks"],
-        "clocks_mixed": mx["clocks"],
+        "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline_subprocess(args)

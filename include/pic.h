@@ -81,7 +81,15 @@ typedef struct {
   int precision;                /* PIC_FP64 or PIC_MIXED */
   double mixed_tol_floor;       /* PIC_MIXED: tolerances are max(tol, this) */
   int sort_every;               /* counting-sort particles by cell every N steps (0 = never) */
-  void *cuda_stream;            /* cudaStream_t to queue work on */
+  void *cuda_stream;            /* cudaStream_t to queue work on; NULL = a stream the
+                                   context creates (blocking, so it orders itself
+                                   with the legacy default stream) */
+  int inner_warm_start;         /* 0 (default): every map evaluation starts the inner
+                                   Picard iteration from v(p^n); 1: later evaluations
+                                   of a step start from the previous evaluation's
+                                   orbit velocity (fewer inner iterations; H(j) then
+                                   depends on the history at the inner tolerance, so
+                                   use it with inner_tol_scale < 1) */
 } pic_options;
 
 /* Per-step report (Sec. 4.4 diagnostics and solver counters). */

@@ -46,7 +46,7 @@ class Options(C.Structure):
         ("backtrack_levels", C.c_int), ("beta", C.c_double), ("lambda_", C.c_double),
         ("decrease_coef", C.c_double), ("growth_limit", C.c_double), ("tol_abs_ratio", C.c_double),
         ("inner_tol_scale", C.c_double), ("precision", C.c_int), ("mixed_tol_floor", C.c_double),
-        ("sort_every", C.c_int), ("cuda_stream", C.c_void_p),
+        ("sort_every", C.c_int), ("cuda_stream", C.c_void_p), ("inner_warm_start", C.c_int),
     ]
 
 

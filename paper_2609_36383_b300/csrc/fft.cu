@@ -93,6 +93,10 @@ int fft_init(pic_ctx *ctx) {
   }
   CK(cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           kFftSmemElems * (int)sizeof(double2)));
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  if (ctx->num_sms < 1) ctx->num_sms = 1;
   return PIC_OK;
 }
 
@@ -102,14 +106,22 @@ int fft_nd(pic_ctx *ctx, double2 *data, int batch, int sign) {
   for (int a = 0; a < g.dim; a++) {
     int N = g.n[a];
     int lines = g.Ng / N;
-    int lpb = kFftSmemElems / N;
+    // lines per CTA: enough CTAs for two waves over the SMs, whole lines in
+    // shared memory, and (for strided axes) lines adjacent in memory
+    int lpb = (int)(((long long)lines * batch) / (2LL * ctx->num_sms));
+    if (lpb > kFftSmemElems / N) lpb = kFftSmemElems / N;
     if (lpb > lines) lpb = lines;
-    if (a > 0 && lpb > stride) lpb = stride;  // keep a CTA's lines adjacent
+    if (a > 0 && lpb > stride) lpb = stride;
     if (lpb < 1) lpb = 1;
+    int p2 = 1;
+    while (p2 * 2 <= lpb) p2 *= 2;
+    lpb = p2;
+    int threads = lpb * N / 2;
+    threads = threads < 32 ? 32 : (threads > kFftThreads ? kFftThreads : (threads + 31) / 32 * 32);
     dim3 grid((lines + lpb - 1) / lpb, batch);
     size_t smem = sizeof(double2) * (size_t)lpb * N;
-    k_fft_axis<<<grid, kFftThreads, smem, ctx->st>>>(data, g.Ng, N, g.logn[a], stride, lines,
-                                                     lpb, ctx->tw[a], sign > 0 ? 1 : 0);
+    k_fft_axis<<<grid, threads, smem, ctx->st>>>(data, g.Ng, N, g.logn[a], stride, lines, lpb,
+                                                 ctx->tw[a], sign > 0 ? 1 : 0);
     KCHECK();
     stride *= N;
   }

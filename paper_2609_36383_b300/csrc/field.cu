@@ -147,15 +147,16 @@ __global__ void k_cn_update(CnArgs p, SpecGeom sg) {
   }
 }
 
+// Node records [grad phi^{1/2} (d), A^n (3), A^{n+1} (3)] padded to nvp reals
+// (a multiple of four), and U^{1/2} records padded to four reals.
 template <typename T>
 __global__ void k_pack_nodes(const double2 *__restrict__ spec, const double *__restrict__ A_n,
                              double *__restrict__ A1_real, T *__restrict__ nodes,
-                             T *__restrict__ nodes_u, int Ng, int d, double inv_ng,
+                             T *__restrict__ nodes_u, int Ng, int d, int nvp, double inv_ng,
                              int want_uhalf) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= Ng) return;
-  const int NV = d + 6;
-  T *rec = nodes + (size_t)g * NV;
+  T *rec = nodes + (size_t)g * nvp;
   for (int c = 0; c < d; c++) rec[c] = (T)(spec[(size_t)c * Ng + g].x * inv_ng);
   for (int c = 0; c < 3; c++) {
     rec[d + c] = (T)A_n[(size_t)c * Ng + g];
@@ -163,9 +164,12 @@ __global__ void k_pack_nodes(const double2 *__restrict__ spec, const double *__r
     rec[d + 3 + c] = (T)a1;
     A1_real[(size_t)c * Ng + g] = a1;
   }
-  if (want_uhalf)
+  for (int c = d + 6; c < nvp; c++) rec[c] = (T)0;
+  if (want_uhalf) {
     for (int c = 0; c < 3; c++)
-      nodes_u[(size_t)g * 3 + c] = (T)(spec[(size_t)(d + 3 + c) * Ng + g].x * inv_ng);
+      nodes_u[(size_t)g * 4 + c] = (T)(spec[(size_t)(d + 3 + c) * Ng + g].x * inv_ng);
+    nodes_u[(size_t)g * 4 + 3] = (T)0;
+  }
 }
 
 // phi^0 from Gauss (k^2 phi = sigma1 rho + i k . U) and psi^0 from the
@@ -283,6 +287,54 @@ __global__ void k_mesh_work_parts(const double2 *Jh, const double2 *phi0, const 
   block_sum_write<1>(v, out);
 }
 
+// (I - Q_a) f along one axis, where Q_a f = c (-1)^n on every line along a
+// with c the alternating mean (1/N) sum_n f_n (-1)^n: the projection onto the
+// modes with k_a = N_a/2.  The product of these factors over the active axes
+// is the projector of Eq. nyquist-projector (the Q_a commute), so applying
+// one kernel per axis projects a real mesh field without a Fourier round trip.
+// One CTA per line; in-place when src == dst.
+__global__ void k_nyq_axis(const double *src, double *dst, int Ng, int N, int stride) {
+  __shared__ double sh[kThreads / 32];
+  const int ln = blockIdx.x;
+  const double *in = src + (size_t)blockIdx.y * Ng;
+  double *out = dst + (size_t)blockIdx.y * Ng;
+  const size_t base = (size_t)(ln % stride) + (size_t)(ln / stride) * stride * N;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    double v = in[base + (size_t)k * stride];
+    s += (k & 1) ? -v : v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double c = 0.0;
+  for (int w = 0; w < (int)(blockDim.x / 32); w++) c += sh[w];
+  c /= N;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    size_t a = base + (size_t)k * stride;
+    out[a] = in[a] - ((k & 1) ? -c : c);
+  }
+}
+
+// sum_g H . E^{1/2} over the mesh in real space, with E^{1/2} = -grad phi^{1/2}
+// - U^{1/2} read from the inverse-transformed gather spectra (real parts,
+// scaled by 1/Ng)
+__global__ void k_mesh_work_real(const double *H, const double2 *spec, int Ng, int d,
+                                 double inv_ng, double *out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (g < Ng) {
+    double s = 0.0;
+    for (int c = 0; c < 3; c++) {
+      double E = -spec[(size_t)(d + 3 + c) * Ng + g].x * inv_ng;
+      if (c < d) E -= spec[(size_t)c * Ng + g].x * inv_ng;
+      s += H[(size_t)c * Ng + g] * E;
+    }
+    v[0] = s;
+  }
+  block_sum_write<1>(v, out);
+}
+
 template <int NQ>
 __global__ void k_sum_partials(const double *parts, int nblk, double *out) {
   // one block; fixed summation order for run-to-run reproducibility
@@ -364,11 +416,11 @@ int field_pack_nodes(pic_ctx *ctx, int want_uhalf) {
   if (ctx->rsize == 8)
     k_pack_nodes<double><<<blocks(Ng), kThreads, 0, ctx->st>>>(
         ctx->work_h, ctx->A_real, ctx->A1_real, (double *)ctx->nodes, (double *)ctx->nodes_u, Ng,
-        d, inv, want_uhalf);
+        d, node_record_len(d), inv, want_uhalf);
   else
     k_pack_nodes<float><<<blocks(Ng), kThreads, 0, ctx->st>>>(
         ctx->work_h, ctx->A_real, ctx->A1_real, (float *)ctx->nodes, (float *)ctx->nodes_u, Ng, d,
-        inv, want_uhalf);
+        node_record_len(d), inv, want_uhalf);
   KCHECK();
   return PIC_OK;
 }
@@ -408,6 +460,42 @@ int field_constraints(pic_ctx *ctx, double *gauss_rms, double *lorenz_rms) {
   if (e) return e;
   *gauss_rms = std::sqrt(s[0]) / ctx->g.Ng;
   *lorenz_rms = std::sqrt(s[1]) / ctx->g.Ng;
+  return PIC_OK;
+}
+
+int field_project_real(pic_ctx *ctx, const double *src, double *dst, int ncomp) {
+  const Geom &g = ctx->g;
+  if (!ctx->opt.project_nyquist) {
+    if (src != dst)
+      CK(cudaMemcpyAsync(dst, src, sizeof(double) * ncomp * g.Ng, cudaMemcpyDeviceToDevice,
+                         ctx->st));
+    return PIC_OK;
+  }
+  int stride = 1;
+  const double *in = src;
+  for (int a = 0; a < g.dim; a++) {
+    int N = g.n[a];
+    int threads = N >= kThreads ? kThreads : (N < 32 ? 32 : N);
+    dim3 grid(g.Ng / N, ncomp);
+    k_nyq_axis<<<grid, threads, 0, ctx->st>>>(in, dst, g.Ng, N, stride);
+    KCHECK();
+    in = dst;
+    stride *= N;
+  }
+  return PIC_OK;
+}
+
+// real-space mesh work of the last (final-pass) evaluation: H and the
+// inverse-transformed gather spectra still in work_h
+int field_mesh_work_real(pic_ctx *ctx, const double *H, double *work) {
+  int nb = blocks(ctx->g.Ng);
+  k_mesh_work_real<<<nb, kThreads, 0, ctx->st>>>(H, ctx->work_h, ctx->g.Ng, ctx->g.dim,
+                                                 1.0 / ctx->g.Ng, ctx->red);
+  KCHECK();
+  double s;
+  int e = finish_sum<1>(ctx, nb, &s);
+  if (e) return e;
+  *work = s * ctx->g.dV;
   return PIC_OK;
 }
 

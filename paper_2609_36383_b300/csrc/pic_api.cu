@@ -60,10 +60,12 @@ void free_all(pic_ctx *ctx) {
                   ctx->phi1_h, ctx->psi1_h, ctx->rho1_h, ctx->A1_h, ctx->U1_h, ctx->jh,
                   ctx->work_h, ctx->A1_real, ctx->scr_r, ctx->nodes, ctx->nodes_u, ctx->Jorb,
                   ctx->Jorb_h, ctx->H, ctx->j, ctx->r, ctx->jt, ctx->Ht, ctx->rt, ctx->dir,
-                  ctx->dJ, ctx->dR, ctx->tw[0], ctx->tw[1], ctx->tw[2], ctx->red, ctx->cnt_dev};
+                  ctx->dJ, ctx->dR, ctx->tw[0], ctx->tw[1], ctx->tw[2], ctx->red, ctx->cnt_dev,
+                  ctx->A_real_f, ctx->cnt_sort, ctx->keys, ctx->tmp_l};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->red_host) cudaFreeHost(ctx->red_host);
+  if (ctx->psum_host) cudaFreeHost(ctx->psum_host);
   if (ctx->cnt_host) cudaFreeHost(ctx->cnt_host);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -82,11 +84,13 @@ int alloc_mesh(pic_ctx *ctx) {
                        &ctx->r, &ctx->jt, &ctx->Ht, &ctx->rt, &ctx->dir};
   for (double **b : rbufs3) CK(cudaMalloc((void **)b, R * 3 * Ng));
   CK(cudaMalloc((void **)&ctx->scr_r, R * 4 * Ng));
+  CK(cudaMalloc((void **)&ctx->cnt_sort, sizeof(int32_t) * Ng));
+  if (ctx->rsize == 4) CK(cudaMalloc(&ctx->A_real_f, sizeof(float) * 3 * Ng));
   int M = std::max(ctx->opt.anderson_m, 1);
   CK(cudaMalloc((void **)&ctx->dJ, R * 3 * Ng * M));
   CK(cudaMalloc((void **)&ctx->dR, R * 3 * Ng * M));
-  CK(cudaMalloc(&ctx->nodes, (size_t)ctx->rsize * (d + 6) * Ng));
-  CK(cudaMalloc(&ctx->nodes_u, (size_t)ctx->rsize * 3 * Ng));
+  CK(cudaMalloc(&ctx->nodes, (size_t)ctx->rsize * node_record_len((int)d) * Ng));
+  CK(cudaMalloc(&ctx->nodes_u, (size_t)ctx->rsize * 4 * Ng));
   size_t nred = 2 * (Ng / 256 + 2) + 1024 * 48 + 64;
   CK(cudaMalloc((void **)&ctx->red, R * nred));
   CK(cudaMallocHost((void **)&ctx->red_host, R * 64));
@@ -131,6 +135,7 @@ StepConst make_sc(const pic_ctx *ctx, double itr, double ita) {
   sc.tau_a = ita;
   sc.inner_max = ctx->opt.inner_max;
   sc.ngl = ctx->opt.gl_points > 0 ? ctx->opt.gl_points : ctx->g.dim + 1;
+  sc.warm = ctx->opt.inner_warm_start ? 1 : 0;
   gauss_legendre01(sc.ngl, sc.gl_t, sc.gl_w);
   return sc;
 }
@@ -140,11 +145,17 @@ struct Eval {
   double work_p, chain;
 };
 
-// One map evaluation H(j) = P J_orb(j) (Sec. 4.5): project the trial
-// current, continuity + CN in Fourier space, inner particle solves, orbit
-// deposit, projection of the deposit.
-int eval_map(pic_ctx *ctx, const double *jdev, double *Hdev, const StepConst &sc, int final_pass,
-             Eval *ev) {
+struct Tests {
+  double srms, smax, rms_r;
+};
+
+// The launch sequence of one map evaluation H(j) = P J_orb(j) (Sec. 4.5):
+// project the trial current, continuity + CN in Fourier space, inner particle
+// solves, orbit deposit, projection of the deposit, then r = H - j and the
+// sums of the outer tests (Eq. mixed-nonlinear-tests).  Nothing here waits
+// for the device, so the sequence can be captured into a CUDA graph.
+int eval_enqueue(pic_ctx *ctx, const double *jdev, double *Hdev, double *rdev,
+                 const StepConst &sc, int final_pass, double tr, double ta) {
   const int Ng = ctx->g.Ng;
   int e;
   if ((e = field_real_to_complex(ctx, jdev, ctx->jh, 3))) return e;
@@ -152,35 +163,90 @@ int eval_map(pic_ctx *ctx, const double *jdev, double *Hdev, const StepConst &sc
   if ((e = field_cn_update(ctx, ctx->jh, final_pass))) return e;
   if ((e = field_pack_nodes(ctx, final_pass))) return e;
   CK(cudaMemsetAsync(ctx->Jorb, 0, sizeof(double) * 3 * Ng, ctx->st));
-  if ((e = particles_map(ctx, sc, final_pass, &ev->work_p, &ev->chain, &ev->cnt))) return e;
+  if ((e = particles_map_launch(ctx, sc, final_pass))) return e;
+  // H = P J_orb with the real-space form of the Nyquist projector
+  if ((e = field_project_real(ctx, ctx->Jorb, Hdev, 3))) return e;
+  if ((e = resid_launch(ctx, Hdev, jdev, rdev, tr, ta))) return e;
+  return PIC_OK;
+}
+
+}  // namespace
+
+void graphs_clear(pic_ctx *ctx) {
+  for (int k = 0; k < ctx->ngraphs; k++) cudaGraphExecDestroy(ctx->graphs[k].exec);
+  ctx->ngraphs = 0;
+}
+
+namespace {
+
+// Queue one evaluation: replay its captured graph when this buffer set,
+// pass kind and tolerance were seen before, otherwise capture it (falling back
+// to direct launches if the stream cannot be captured).
+int eval_launch(pic_ctx *ctx, const double *jdev, double *Hdev, double *rdev,
+                const StepConst &sc, int final_pass, double tr, double ta) {
+  ctx->map_final = final_pass;
+  if (ctx->graphs_off || ctx->np == 0)
+    return eval_enqueue(ctx, jdev, Hdev, rdev, sc, final_pass, tr, ta);
+  for (int k = 0; k < ctx->ngraphs; k++) {
+    const pic_ctx::GraphEntry &g = ctx->graphs[k];
+    if (g.j == jdev && g.H == Hdev && g.r == rdev && g.phi == ctx->phi_h && g.A == ctx->A_real &&
+        g.final_pass == final_pass && g.tr == tr && g.ta == ta && g.itr == sc.tau_r &&
+        g.ita == sc.tau_a && g.np == ctx->np) {
+      CK(cudaGraphLaunch(g.exec, ctx->st));
+      ctx->launches += g.nkern;
+      return PIC_OK;
+    }
+  }
+  if (ctx->ngraphs == 16) graphs_clear(ctx);
+  long long before = ctx->launches;
+  if (cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->graphs_off = 1;
+    return eval_enqueue(ctx, jdev, Hdev, rdev, sc, final_pass, tr, ta);
+  }
+  int e = eval_enqueue(ctx, jdev, Hdev, rdev, sc, final_pass, tr, ta);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(ctx->st, &graph);
+  if (e || ce != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    ctx->graphs_off = 1;
+    ctx->launches = before;
+    if (e && e != PIC_ECUDA) return e;
+    return eval_enqueue(ctx, jdev, Hdev, rdev, sc, final_pass, tr, ta);
+  }
+  cudaGraphExec_t exec = nullptr;
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    ctx->graphs_off = 1;
+    ctx->launches = before;
+    return eval_enqueue(ctx, jdev, Hdev, rdev, sc, final_pass, tr, ta);
+  }
+  pic_ctx::GraphEntry &g = ctx->graphs[ctx->ngraphs++];
+  g.j = jdev; g.H = Hdev; g.r = rdev; g.phi = ctx->phi_h; g.A = ctx->A_real;
+  g.final_pass = final_pass; g.tr = tr; g.ta = ta; g.itr = sc.tau_r; g.ita = sc.tau_a;
+  g.np = ctx->np;
+  g.nkern = (int)(ctx->launches - before);
+  g.exec = exec;
+  CK(cudaGraphLaunch(exec, ctx->st));
+  return PIC_OK;
+}
+
+// One evaluation: queue it, wait once, read the counters and the test sums.
+int eval_map(pic_ctx *ctx, const double *jdev, double *Hdev, double *rdev, const StepConst &sc,
+             int final_pass, double tr, double ta, Eval *ev, Tests *t) {
+  int e;
+  if ((e = eval_launch(ctx, jdev, Hdev, rdev, sc, final_pass, tr, ta))) return e;
+  CK(cudaStreamSynchronize(ctx->st));
+  if ((e = particles_map_finish(ctx, &ev->work_p, &ev->chain, &ev->cnt))) return e;
   if (ev->cnt.status) {
     ctx->err = "inner particle solve failed (status bits " + std::to_string(ev->cnt.status) + ")";
     return PIC_EINNER;
   }
-  if ((e = field_real_to_complex(ctx, ctx->Jorb, ctx->Jorb_h, 3))) return e;
-  if ((e = fft_nd(ctx, ctx->Jorb_h, 3, -1))) return e;
-  if ((e = field_project_h(ctx, ctx->Jorb_h, 3))) return e;
-  if (ctx->opt.project_nyquist) {
-    CK(cudaMemcpyAsync(ctx->work_h, ctx->Jorb_h, sizeof(double2) * 3 * Ng,
-                       cudaMemcpyDeviceToDevice, ctx->st));
-    if ((e = fft_nd(ctx, ctx->work_h, 3, +1))) return e;
-    if ((e = field_complex_to_real(ctx, ctx->work_h, Hdev, 3, 1.0 / Ng))) return e;
-  } else {
-    CK(cudaMemcpyAsync(Hdev, ctx->Jorb, sizeof(double) * 3 * Ng, cudaMemcpyDeviceToDevice,
-                       ctx->st));
-  }
-  return PIC_OK;
-}
-
-struct Tests {
-  double srms, smax, rms_r;
-};
-
-int run_tests(pic_ctx *ctx, const double *H, const double *j, double *r, double tr, double ta,
-              Tests *t) {
   ResidSums s;
-  int e = resid_sums(ctx, H, j, r, tr, ta, &s);
-  if (e) return e;
+  resid_finish(ctx, &s);
   double n3 = 3.0 * ctx->g.Ng;
   t->rms_r = std::sqrt(s.r2 / n3);
   t->srms = t->rms_r / (ta + 0.5 * tr * (std::sqrt(s.H2 / n3) + std::sqrt(s.j2 / n3)));
@@ -283,8 +349,9 @@ void pic_default_options(pic_options *o) {
   o->inner_tol_scale = 1.0;
   o->precision = PIC_FP64;
   o->mixed_tol_floor = 1e-5;
-  o->sort_every = 0;
+  o->sort_every = 10;
   o->cuda_stream = nullptr;
+  o->inner_warm_start = 0;
 }
 
 int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, int nspecies,
@@ -311,6 +378,15 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, in
   if (!ctx) return PIC_ENOMEM;
   ctx->opt = o;
   ctx->st = (cudaStream_t)o.cuda_stream;
+  if (!ctx->st) {
+    // the legacy default stream cannot be captured into graphs: use a
+    // blocking stream of our own, which orders itself with the legacy stream
+    if (cudaStreamCreate(&ctx->own_st) != cudaSuccess) {
+      delete ctx;
+      return PIC_ECUDA;
+    }
+    ctx->st = ctx->own_st;
+  }
   ctx->dt = dt;
   ctx->nspecies = nspecies;
   for (int s = 0; s < nspecies; s++) {
@@ -337,6 +413,7 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, in
   if (!e) e = particles_alloc(ctx, 1);
   if (e) {
     free_all(ctx);
+    if (ctx->own_st) cudaStreamDestroy(ctx->own_st);
     delete ctx;
     return e == PIC_ECUDA ? PIC_ENOMEM : e;
   }
@@ -347,7 +424,9 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, in
 void pic_free(pic_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->st);
+  graphs_clear(ctx);
   free_all(ctx);
+  if (ctx->own_st) cudaStreamDestroy(ctx->own_st);
   delete ctx;
 }
 
@@ -386,6 +465,7 @@ int pic_set_particles(pic_ctx *ctx, int64_t n, const int32_t *species, const dou
         ctx->err = "pic_set_particles: species index out of range";
         return PIC_EARG;
       }
+  graphs_clear(ctx);
   int e = particles_alloc(ctx, n);
   if (e) return e;
   ctx->np = n;
@@ -422,6 +502,7 @@ int pic_start(pic_ctx *ctx, pic_report *out) {
                      ctx->st));
   if ((e = fft_nd(ctx, ctx->work_h, 3, +1))) return e;
   if ((e = field_complex_to_real(ctx, ctx->work_h, ctx->A_real, 3, 1.0 / Ng))) return e;
+  if ((e = particles_refresh_A(ctx))) return e;
   if (ctx->pending_mech) {
     if ((e = particles_form_P(ctx))) return e;
     ctx->pending_mech = 0;
@@ -448,6 +529,7 @@ int pic_start(pic_ctx *ctx, pic_report *out) {
   if ((e = finish_report(ctx, &R))) return e;
   ctx->E0 = R.E_tot;
   R.rel_dE = 0.0;
+  if (ctx->opt.sort_every > 0 && (e = particles_sort(ctx))) return e;
   ctx->started = 1;
   ctx->steps_done = 0;
   if (out) *out = R;
@@ -471,7 +553,8 @@ int pic_eval_map(pic_ctx *ctx, const double *j, double tol, double *H, double *v
   else CK(cudaMemcpyAsync(ctx->jt, ctx->J_acc, sizeof(double) * N3, cudaMemcpyDeviceToDevice,
                           ctx->st));
   Eval ev;
-  int st = eval_map(ctx, ctx->jt, ctx->Ht, sc, 0, &ev);
+  Tests T;
+  int st = eval_map(ctx, ctx->jt, ctx->Ht, ctx->rt, sc, 0, tr, ta, &ev, &T);
   if (st != PIC_OK && st != PIC_EINNER) return st;
   if (H && st == PIC_OK)
     CK(cudaMemcpyAsync(H, ctx->Ht, sizeof(double) * N3,
@@ -501,11 +584,10 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
   double *j = ctx->j, *H = ctx->H, *r = ctx->r, *jt = ctx->jt, *Ht = ctx->Ht, *rt = ctx->rt;
   CK(cudaMemcpyAsync(j, ctx->J_acc, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
   Eval ev;
-  int status = eval_map(ctx, j, H, sc, 0, &ev);
+  Tests T;
+  int status = eval_map(ctx, j, H, r, sc, 0, tr, ta, &ev, &T);
   R.map_evals = 1;
   if (status != PIC_OK && status != PIC_EINNER) return status;
-  Tests T;
-  if (status == PIC_OK && (e = run_tests(ctx, H, j, r, tr, ta, &T))) return e;
   // Anderson history: ring of M columns, oldest at hist0
   int mh = 0, hist0 = 0;
   bool done = false;
@@ -515,10 +597,9 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
     R.res_scaled_max = T.smax;
     if (T.srms <= 1.0 && T.smax <= 1.0) {
       // verify by re-evaluating the map at the candidate current
-      status = eval_map(ctx, j, H, sc, 1, &ev);
+      status = eval_map(ctx, j, H, r, sc, 1, tr, ta, &ev, &T);
       R.map_evals++;
       if (status != PIC_OK) break;
-      if ((e = run_tests(ctx, H, j, r, tr, ta, &T))) return e;
       R.res_scaled_rms = T.srms;
       R.res_scaled_max = T.smax;
       if (!(T.srms <= 1.0 && T.smax <= 1.0)) {
@@ -564,10 +645,9 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
       double alpha = 1.0;
       for (int lvl = 0; lvl < ctx->opt.backtrack_levels; lvl++, alpha *= 0.5) {
         if ((e = lincomb(ctx, jt, j, 1.0, ctx->dir, alpha, N3))) return e;
-        status = eval_map(ctx, jt, Ht, sc, 0, &ev);
+        status = eval_map(ctx, jt, Ht, rt, sc, 0, tr, ta, &ev, &Tt);
         R.map_evals++;
         if (status != PIC_OK) break;
-        if ((e = run_tests(ctx, Ht, jt, rt, tr, ta, &Tt))) return e;
         if (Tt.srms <= (1.0 - ctx->opt.decrease_coef * alpha) * T.srms &&
             Tt.smax <= ctx->opt.growth_limit * T.smax) {
           accepted = true;
@@ -608,7 +688,7 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
   ctx->j = j; ctx->H = H; ctx->r = r; ctx->jt = jt; ctx->Ht = Ht; ctx->rt = rt;
   if (status == PIC_OK) {
     double mesh_work;
-    if ((e = field_mesh_work(ctx, &mesh_work))) return e;
+    if ((e = field_mesh_work_real(ctx, H, &mesh_work))) return e;
     R.work_residual = ctx->dt * (ev.work_p - mesh_work);
     R.chain_rms = ctx->np ? std::sqrt(ev.chain / (3.0 * ctx->np)) : 0.0;
     R.inner_max = ev.cnt.inner_max;
@@ -620,9 +700,13 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
     std::swap(ctx->A_h, ctx->A1_h);
     std::swap(ctx->U_h, ctx->U1_h);
     std::swap(ctx->A_real, ctx->A1_real);
+    if ((e = particles_refresh_A(ctx))) return e;
     CK(cudaMemcpyAsync(ctx->J_acc, j, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
     if ((e = finish_report(ctx, &R))) return e;
     ctx->steps_done++;
+    if (ctx->opt.sort_every > 0 && ctx->steps_done % ctx->opt.sort_every == 0 &&
+        (e = particles_sort(ctx)))
+      return e;
   }
   R.status = status;
   if (out) *out = R;
@@ -677,6 +761,7 @@ int pic_set_state(pic_ctx *ctx, int64_t n, const int32_t *species, const double 
     }
   }
   if ((e = copy_in(ctx, ctx->A_real, A, 3 * Ng, on_device))) return e;
+  if ((e = particles_refresh_A(ctx))) return e;
   if ((e = copy_in(ctx, ctx->J_acc, J, 3 * Ng, on_device))) return e;
   CK(cudaStreamSynchronize(ctx->st));
   ctx->E0 = E0;

@@ -19,6 +19,10 @@
 #define PIC_ST_SUPERLUM 4u    // |vbar| >= kappa
 #define PIC_ST_PIECES 8u      // orbit crosses more knots than the kernel handles
 
+// reals per gather record: [grad phi^{1/2} (d), A^n (3), A^{n+1} (3)] padded
+// to a multiple of four so that records load with 16-byte vector loads
+inline int node_record_len(int d) { return (d + 6 + 3) / 4 * 4; }
+
 struct Geom {
   int dim;
   int n[3];
@@ -34,6 +38,7 @@ struct StepConst {
   double tau_r, tau_a;  // inner tolerances
   int inner_max;
   int ngl;
+  int warm;  // start the inner iteration from vbar instead of v^0
   double gl_t[PIC_MAX_GL], gl_w[PIC_MAX_GL];  // nodes and weights on [0, 1]
 };
 
@@ -42,6 +47,7 @@ struct EvalCounters {
   unsigned int status;
   int inner_max;
   unsigned long long inner_sum;
+  unsigned long long pieces;
 };
 
 // Reduction partials returned to the host after the residual kernel.
@@ -76,7 +82,8 @@ struct pic_ctx {
   int32_t *iters;     // [cap]
   double *u_in;       // [3][cap] mechanical input awaiting pic_start
   // sort scratch
-  int32_t *keys, *cnt;
+  int32_t *keys;      // [cap] sort keys
+  int32_t *cnt_sort;  // [Ng] per-cell counts / cursors of the sort
   void *tmp_r;        // [3][cap] scratch of particle reals
   double *tmp_d;      // [3][cap]
   int32_t *tmp_i;     // [3][cap]
@@ -85,6 +92,7 @@ struct pic_ctx {
   // ---- mesh: accepted state (spectral primary + real copies) ------------
   double2 *phi_h, *psi_h, *rho_h, *A_h, *U_h;   // Ng, Ng, Ng, 3Ng, 3Ng
   double *A_real;     // 3Ng  A^n in real space (gather)
+  void *A_real_f;     // 3Ng  float copy of A^n (mixed path only)
   double *J_acc;      // 3Ng  accepted current (seed of the next outer solve)
   // ---- mesh: one map evaluation -----------------------------------------
   double2 *phi1_h, *psi1_h, *rho1_h, *A1_h, *U1_h;  // n+1 candidates
@@ -107,6 +115,8 @@ struct pic_ctx {
   double *red_host;   // pinned
   EvalCounters *cnt_dev, *cnt_host;
   double *psum;       // per-block particle sums (work, chain, K)
+  double *psum_host;  // pinned copy of the final-pass partials
+  int map_final;      // the queued particle map is a final (diagnostic) pass
   // ---- statistics (pic_stats) ------------------------------------------
   long long launches;          // kernels launched by this context
   long long map_launches;      // particle-map kernel launches
@@ -115,7 +125,24 @@ struct pic_ctx {
   long long inner_iters;       // summed inner iterations
   long long pieces;            // summed knot-split orbit pieces walked
   cudaEvent_t ev0, ev1;
+  int num_sms;
+  // ---- execution -----------------------------------------------------------
+  cudaStream_t own_st;  // created when the caller passed no stream
+  struct GraphEntry {
+    const void *j, *H, *r, *phi, *A;
+    int final_pass;
+    double tr, ta, itr, ita;
+    int64_t np;
+    int nkern;  // kernels in the graph
+    cudaGraphExec_t exec;
+  };
+  GraphEntry graphs[16];
+  int ngraphs;
+  int graphs_off;  // capture failed once: launch directly
 };
+
+// drop every captured graph (buffers or sizes changed)
+void graphs_clear(pic_ctx *ctx);
 
 // every kernel launch is followed by KCHECK(): it counts the launch and
 // turns a launch error into PIC_ECUDA
@@ -152,6 +179,9 @@ int field_energy(pic_ctx *ctx, const double2 *phi_h, const double2 *A_h,
                  const double2 *U_h, double *W);
 int field_constraints(pic_ctx *ctx, double *gauss_rms, double *lorenz_rms);
 int field_mesh_work(pic_ctx *ctx, double *work);
+// Nyquist projection of ncomp real mesh arrays (src may equal dst)
+int field_project_real(pic_ctx *ctx, const double *src, double *dst, int ncomp);
+int field_mesh_work_real(pic_ctx *ctx, const double *H, double *work);
 
 // ---------------------------------------------------------------- particle.cu
 int particles_alloc(pic_ctx *ctx, int64_t n);
@@ -160,10 +190,14 @@ int particles_load(pic_ctx *ctx, const int32_t *sp, const double *x, const doubl
 int particles_form_P(pic_ctx *ctx);
 int particles_point_deposit(pic_ctx *ctx, double *rho, double *J);
 int particles_step_start(pic_ctx *ctx);
-int particles_map(pic_ctx *ctx, const StepConst &sc, int final_pass, double *work_sum,
-                  double *chain_sum, EvalCounters *cnt);
+// queue the particle map and the copies of its counters and sums to pinned
+// host memory; particles_map_finish reads them after the stream is synced
+int particles_map_launch(pic_ctx *ctx, const StepConst &sc, int final_pass);
+int particles_map_finish(pic_ctx *ctx, double *work_sum, double *chain_sum, EvalCounters *cnt);
 int particles_commit(pic_ctx *ctx);
 int particles_kinetic(pic_ctx *ctx, double *K);
+// refresh the particle-precision copy of A^n after A_real changed
+int particles_refresh_A(pic_ctx *ctx);
 int particles_export(pic_ctx *ctx, double *x, double *P, double *w, int32_t *sp,
                      int on_device);
 int particles_export_eval(pic_ctx *ctx, double *vbar, double *Pnew, int32_t *iters,
@@ -171,8 +205,11 @@ int particles_export_eval(pic_ctx *ctx, double *vbar, double *Pnew, int32_t *ite
 int particles_sort(pic_ctx *ctx);
 
 // ---------------------------------------------------------------- reduce.cu
-int resid_sums(pic_ctx *ctx, const double *Hv, const double *jv, double *rv, double tau_r,
-               double tau_a, ResidSums *out);
+// queue r = H - j and its test sums (copied to pinned host memory);
+// resid_finish reads them after the stream is synced
+int resid_launch(pic_ctx *ctx, const double *Hv, const double *jv, double *rv, double tau_r,
+                 double tau_a);
+void resid_finish(pic_ctx *ctx, ResidSums *out);
 int dots(pic_ctx *ctx, const double *const *a, const double *const *b, int npairs, double *out);
 int axpy_dir(pic_ctx *ctx, double *dir, const double *r, double beta,
              const double *const *dJ, const double *const *dR, const double *gam, int mh,

@@ -155,8 +155,8 @@ int grid_for(size_t n) {
 
 }  // namespace
 
-int resid_sums(pic_ctx *ctx, const double *Hv, const double *jv, double *rv, double tau_r,
-               double tau_a, ResidSums *out) {
+int resid_launch(pic_ctx *ctx, const double *Hv, const double *jv, double *rv, double tau_r,
+                 double tau_a) {
   int Ng = ctx->g.Ng;
   int nb = grid_for(Ng);
   k_resid<<<nb, kT, 0, ctx->st>>>(Hv, jv, rv, Ng, tau_r, tau_a, ctx->red);
@@ -165,12 +165,14 @@ int resid_sums(pic_ctx *ctx, const double *Hv, const double *jv, double *rv, dou
   KCHECK();
   CK(cudaMemcpyAsync(ctx->red_host, ctx->red + (size_t)nb * 4, sizeof(double) * 4,
                      cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
+  return PIC_OK;
+}
+
+void resid_finish(pic_ctx *ctx, ResidSums *out) {
   out->r2 = ctx->red_host[0];
   out->H2 = ctx->red_host[1];
   out->j2 = ctx->red_host[2];
   out->smax = ctx->red_host[3];
-  return PIC_OK;
 }
 
 int dots(pic_ctx *ctx, const double *const *a, const double *const *b, int npairs, double *out) {

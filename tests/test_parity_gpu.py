@@ -144,6 +144,27 @@ def test_free_running_steps_parity_and_energy(case):
     _field_close(s.fields(), o.fields(), 1e-9, cfg)
 
 
+def test_cell_sort_does_not_change_results():
+    """Counting-sorting the particles by cell (every step vs never) changes only
+    the summation order of the deposit: results agree at roundoff."""
+    cfg = _ragged_2d()
+    a = make_gpu(cfg, sort_every=1)
+    b = make_gpu(cfg, sort_every=0)
+    a.start()
+    b.start()
+    for _ in range(3):
+        ra = a.step(1e-12)
+        rb = b.step(1e-12)
+        assert ra["status"] == 0 and rb["status"] == 0
+        assert ra["E_tot"] == pytest.approx(rb["E_tot"], rel=1e-13)
+    xa, Pa, wa, sa = a.particles()
+    xb, Pb, wb, sb = b.particles()
+    assert np.abs(periodic_diff(xa, xb, cfg["L"])).max() < 1e-9 * max(cfg["L"])
+    assert rel_err(Pa, Pb) < 1e-9
+    assert np.array_equal(wa, wb) and np.array_equal(sa, sb)
+    _field_close(a.fields(), b.fields(), 1e-9, cfg)
+
+
 def test_failed_step_leaves_state_unchanged():
     cfg = small_2d()
     s = make_gpu(cfg)
