@@ -132,6 +132,25 @@ __device__ __forceinline__ int node_index(const PGeom &pg, const int cell[3], co
   return g;
 }
 
+// Wrapped node coordinates of the 3 nodes around base along each active
+// dimension, pre-scaled by the dimension's stride: node (ox, oy, oz) is
+// gx[ox] + gy[oy] + gz[oz].
+template <int D>
+struct NodeRows {
+  int gx[3], gy[3], gz[3];
+  __device__ __forceinline__ NodeRows(const PGeom &pg, const int cell[3], const int base[3]) {
+#pragma unroll
+    for (int o = 0; o < 3; o++) {
+      gx[o] = (cell[0] + base[0] + o - 1) & pg.mask[0];
+      gy[o] = D > 1 ? pg.n0 * ((cell[1] + base[1] + o - 1) & pg.mask[1]) : 0;
+      gz[o] = D > 2 ? pg.n01 * ((cell[2] + base[2] + o - 1) & pg.mask[2]) : 0;
+    }
+  }
+  __device__ __forceinline__ int at(int ox, int oy, int oz) const {
+    return gx[ox] + (D > 1 ? gy[oy] : 0) + (D > 2 ? gz[oz] : 0);
+  }
+};
+
 // Walks the knot-split pieces of the straight orbit u(s) = off + s del,
 // s in [0, 1], calling f(base, sa, sb) on each piece, where base is the node
 // (relative to the particle's cell) nearest to u inside the piece.  Returns
@@ -300,6 +319,53 @@ __device__ __forceinline__ void accumulate_piece(const KConst<T> &kc, const T of
   }
 }
 
+// 3D: the same orbit integrals for the 9 nodes (ox, oy) of one z-slab oz of
+// the 27-node stencil, so that the accumulators of a slab (9 x 7 values) fit
+// in registers; the caller loops over the three slabs and contracts each.
+template <typename T, bool DERIV>
+__device__ __forceinline__ void accumulate_slab(const KConst<T> &kc, const T off[3],
+                                                const T del[3], const int base[3], T sa, T sb,
+                                                int oz, PieceAcc<2, T> &pa, T (&Wz)[9],
+                                                T (&W1z)[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    pa.Sb[k] = T(0);
+    pa.Wd[0][k] = pa.W1[0][k] = pa.Wd[1][k] = pa.W1[1][k] = T(0);
+    Wz[k] = W1z[k] = T(0);
+  }
+  const T len = sb - sa;
+  T t0[3];
+#pragma unroll
+  for (int l = 0; l < 3; l++) t0[l] = off[l] - T(base[l]);
+#pragma unroll 1
+  for (int qp = 0; qp < kc.ngl; qp++) {
+    const T s = sa + len * kc.gl_t[qp];
+    const T wt = len * kc.gl_w[qp];
+    T S[3][3], dS[3][3];
+#pragma unroll
+    for (int l = 0; l < 3; l++) qspline<T>(t0[l] + s * del[l], S[l], dS[l]);
+    const T wz = wt * S[2][oz], wdz = wt * dS[2][oz];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const T a = wz * S[0][i], b = wz * dS[0][i], az = wdz * S[0][i];
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        const int k = i + 3 * j;
+        pa.Sb[k] += a * S[1][j];
+        if (DERIV) {
+          const T d0 = b * S[1][j], d1 = a * dS[1][j], d2 = az * S[1][j];
+          pa.Wd[0][k] += d0;
+          pa.W1[0][k] += s * d0;
+          pa.Wd[1][k] += d1;
+          pa.W1[1][k] += s * d1;
+          Wz[k] += d2;
+          W1z[k] += s * d2;
+        }
+      }
+    }
+  }
+}
+
 // Inner-iteration gather: grad phi-bar (Eq. orbit-gather-general with
 // G = grad phi^{1/2}) and the discrete gradient D (3 x D, node units until
 // the caller scales column j by 1/dx_j).
@@ -316,6 +382,34 @@ struct GatherOrbit {
   __device__ __forceinline__ void operator()(const int base[3], T sa, T sb) {
     constexpr int NVP = Rec<D>::NVP;
     pieces++;
+    const NodeRows<D> nr(*pg, cell, base);
+    if (D == 3) {
+#pragma unroll 1
+      for (int oz = 0; oz < 3; oz++) {
+        PieceAcc<2, T> pa;
+        T Wz[9], W1z[9];
+        accumulate_slab<T, true>(*kc, off, del, base, sa, sb, oz, pa, Wz, W1z);
+#pragma unroll
+        for (int oy = 0; oy < 3; oy++)
+#pragma unroll
+          for (int ox = 0; ox < 3; ox++) {
+            const int k = ox + 3 * oy;
+            const int g = nr.at(ox, oy, oz);
+            T r[NVP];
+            load_rec<NVP>(nodes + (size_t)g * NVP, r);
+#pragma unroll
+            for (int c = 0; c < D; c++) gphi[c] += r[c] * pa.Sb[k];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+              const T An = r[D + c], dA = r[D + 3 + c] - An;
+              Dm[c][0] += An * pa.Wd[0][k] + dA * pa.W1[0][k];
+              Dm[c][1] += An * pa.Wd[1][k] + dA * pa.W1[1][k];
+              Dm[c][D > 2 ? 2 : 0] += An * Wz[k] + dA * W1z[k];
+            }
+          }
+      }
+      return;
+    }
     PieceAcc<D, T> pa;
     accumulate_piece<D, T, true>(*kc, off, del, base, sa, sb, pa);
 #pragma unroll
@@ -324,9 +418,8 @@ struct GatherOrbit {
       for (int oy = 0; oy < (D > 1 ? 3 : 1); oy++)
 #pragma unroll
         for (int ox = 0; ox < 3; ox++) {
-          const int o[3] = {ox - 1, oy - 1, oz - 1};
           const int k = ox + 3 * (oy + 3 * oz);
-          const int g = node_index<D>(*pg, cell, base, o);
+          const int g = nr.at(ox, oy, oz);
           T r[NVP];
           load_rec<NVP>(nodes + (size_t)g * NVP, r);
 #pragma unroll
@@ -380,17 +473,57 @@ struct DepositOrbit {
   __device__ __forceinline__ void operator()(const int base[3], T sa, T sb) {
     constexpr int NVP = Rec<D>::NVP;
     pieces++;
+    const NodeRows<D> nr(*pg, cell, base);
+    if (D == 3) {
+#pragma unroll 1
+      for (int oz = 0; oz < 3; oz++) {
+        PieceAcc<2, T> pa;
+        T Wz[9], W1z[9];
+        accumulate_slab<T, FINAL>(*kc, off, del, base, sa, sb, oz, pa, Wz, W1z);
+#pragma unroll
+        for (int oy = 0; oy < 3; oy++)
+#pragma unroll
+          for (int ox = 0; ox < 3; ox++) {
+            const int k = ox + 3 * oy;
+            const int g = nr.at(ox, oy, oz);
+            if (FINAL) {
+              T r[NVP], u[4];
+              load_rec<NVP>(nodes + (size_t)g * NVP, r);
+              load_rec<4>(nodes_u + (size_t)g * 4, u);
+#pragma unroll
+              for (int c = 0; c < D; c++) gphi[c] += r[c] * pa.Sb[k];
+#pragma unroll
+              for (int c = 0; c < 3; c++) {
+                Ubar[c] += u[c] * pa.Sb[k];
+                const T An = r[D + c], dA = r[D + 3 + c] - An;
+                Dm[c][0] += An * pa.Wd[0][k] + dA * pa.W1[0][k];
+                Dm[c][1] += An * pa.Wd[1][k] + dA * pa.W1[1][k];
+                Dm[c][D > 2 ? 2 : 0] += An * Wz[k] + dA * W1z[k];
+              }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+              atomicAdd(J + (size_t)c * pg->Ng + g, widen(qv[c] * pa.Sb[k]));
+          }
+      }
+      return;
+    }
     PieceAcc<D, T> pa;
     accumulate_piece<D, T, FINAL>(*kc, off, del, base, sa, sb, pa);
+    // window coordinates of the piece's base node (relative to ref)
+    int wx = 0, wy = 0;
+    if (WarpWin<D>::kOn && win) {
+      wx = wrap_rel(cell[0] + base[0] - ref[0], pg->n[0]) - 1 - WarpWin<D>::LO0;
+      wy = D > 1 ? wrap_rel(cell[1] + base[1] - ref[1], pg->n[1]) - 1 - WarpWin<D>::LO1 : 0;
+    }
 #pragma unroll
     for (int oz = 0; oz < (D > 2 ? 3 : 1); oz++)
 #pragma unroll
       for (int oy = 0; oy < (D > 1 ? 3 : 1); oy++)
 #pragma unroll
         for (int ox = 0; ox < 3; ox++) {
-          const int o[3] = {ox - 1, oy - 1, oz - 1};
           const int k = ox + 3 * (oy + 3 * oz);
-          const int g = node_index<D>(*pg, cell, base, o);
+          const int g = nr.at(ox, oy, oz);
           if (FINAL) {
             T r[NVP], u[4];
             load_rec<NVP>(nodes + (size_t)g * NVP, r);
@@ -407,10 +540,7 @@ struct DepositOrbit {
           }
           int e = -1;
           if (WarpWin<D>::kOn && win) {
-            const int rx = wrap_rel(cell[0] + base[0] + o[0] - ref[0], pg->n[0]) - WarpWin<D>::LO0;
-            const int ry = D > 1 ? wrap_rel(cell[1] + base[1] + o[1] - ref[1], pg->n[1]) -
-                                       WarpWin<D>::LO1
-                                 : 0;
+            const int rx = wx + ox, ry = wy + (D > 1 ? oy : 0);
             if (rx >= 0 && rx < WarpWin<D>::N0 && ry >= 0 && ry < WarpWin<D>::N1)
               e = 3 * (rx + WarpWin<D>::N0 * ry);
           }
@@ -438,14 +568,14 @@ __device__ __forceinline__ void interp_A1(const PGeom &pg, const int cell[3], co
     qspline_val<T>(u[l] - T(base[l]), Sw[l]);
   }
   out[0] = out[1] = out[2] = T(0);
+  const NodeRows<D> nr(pg, cell, base);
 #pragma unroll
   for (int oz = 0; oz < (D > 2 ? 3 : 1); oz++)
 #pragma unroll
     for (int oy = 0; oy < (D > 1 ? 3 : 1); oy++)
 #pragma unroll
       for (int ox = 0; ox < 3; ox++) {
-        const int o[3] = {ox - 1, oy - 1, oz - 1};
-        const int g = node_index<D>(pg, cell, base, o);
+        const int g = nr.at(ox, oy, oz);
         T r[NVP];
         load_rec<NVP>(nodes + (size_t)g * NVP, r);
         const T w = Sw[0][ox] * (D > 1 ? Sw[1][oy] : T(1)) * (D > 2 ? Sw[2][oz] : T(1));
@@ -606,8 +736,10 @@ __device__ __forceinline__ void block_sums(double (&v)[NQ], double *out) {
   }
 }
 
+// FP32 instances: at least 4 resident CTAs (<= 128 registers) to hide latency;
+// FP64 instances are bound by the FP64 pipe and keep their registers
 template <int D, typename T, bool FINAL>
-__global__ void __launch_bounds__(kPT)
+__global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 4 : 1)
 k_map(PView<T> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
       double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
       double *__restrict__ psum) {

@@ -184,6 +184,126 @@ def weibel_2d_ions(n=512, ppc_beam=64, ppc_ion=128, u_drift=0.9, T=0.05, mass_ra
                 A=e["A"], U=None)
 
 
+def thermal_box(dim=3, n=8, ppc=2, T=0.05, u_drift=0.3, dt=0.1, tol=1e-12, seed=0,
+                L=2.0 * math.pi, noise=1e-3):
+    """Counter-streaming Maxwell-Juettner beams along z in a periodic box of
+    any dimension (used for parity checks in 1D-3D): uniform random positions
+    per cell, `ppc` particles per cell split between the beams, a random
+    vector-potential seed of amplitude `noise` on every node."""
+    rng = np.random.default_rng(seed)
+    ns = [n] * dim
+    Ls = [L] * dim
+    x0 = [-0.5 * L] * dim
+    ncell = n ** dim
+    cells = np.repeat(np.arange(ncell), ppc)
+    N = cells.shape[0]
+    idx = np.stack(np.unravel_index(cells, ns[::-1])[::-1])  # x fastest
+    x = np.stack([x0[l] + (idx[l] + rng.random(N)) * Ls[l] / n for l in range(dim)])
+    half = N // 2
+    u = np.concatenate([drifting_mj(rng, T, u_drift, 2, half),
+                        drifting_mj(rng, T, -u_drift, 2, N - half)], axis=1)
+    perm = rng.permutation(N)
+    u = u[:, perm]
+    w = np.full(N, float(np.prod(Ls)) / N)
+    A = noise * rng.standard_normal((3, ncell))
+    return dict(name=f"thermal_box_{dim}d_{n}_{ppc}ppc", dim=dim, n=ns, L=Ls, x0=x0,
+                species=[(-1.0, 1.0)], rho_bg=1.0, dt=dt, tol=tol, steps=4,
+                x=x, u=u, w=w, sp=np.zeros(N, np.int32), A=A, U=None)
+
+
+def _quiet_pairs_3d(n, L, x0, pairs):
+    """Pair positions: the same `pairs` sub-cell offsets in every cell (a
+    Weyl sequence in y and z, evenly spaced in x), so that deposits are
+    uniform across cells and no transverse mode is seeded by the loading."""
+    k = np.arange(pairs)
+    sub = np.stack([(k + 0.5) / pairs, (k * 0.6180339887498949 + 0.25) % 1.0,
+                    (k * 0.7548776662466927 + 0.5) % 1.0])
+    ncell = n[0] * n[1] * n[2]
+    cells = np.repeat(np.arange(ncell), pairs)
+    ci = np.stack(np.unravel_index(cells, (n[2], n[1], n[0]))[::-1])
+    return np.stack([x0[l] + (ci[l] + np.tile(sub[l], ncell)) * L[l] / n[l] for l in range(3)])
+
+
+def two_stream_3d(n=32, pairs=10, v0=0.9, alpha=5e-3, dt=0.1, tol=1e-11, steps=600, *,
+                  eigen_rate, eigen_chi):
+    """3D3V cold relativistic two-stream of Sec. 5.1 (TSI, Table 1): [-4 pi, 4 pi]^3,
+    pairs of electrons at +-v0 along x in every cell, seeded with the growing
+    cold-fluid eigenvector whose grid density is alpha rho0 cos(k x) and
+    E_x = (sigma1 alpha rho0 / k) sin(k x), k = 1/4; the particle responses use
+    the gathered field chi_2(k) E_x.  eigen_rate (Gamma_TS) and eigen_chi are
+    inputs, not computed here."""
+    L = [8.0 * math.pi] * 3
+    x0 = [-4.0 * math.pi] * 3
+    ns = [n, n, n]
+    k = 2.0 * math.pi / L[0]
+    xp = _quiet_pairs_3d(ns, L, x0, pairs)
+    m = xp.shape[1]
+    g0 = 1.0 / math.sqrt(1.0 - v0 * v0)
+    om = 1j * eigen_rate
+    Ehat = -1j * alpha / k  # E_x = Re(Ehat e^{ikx}) = (alpha / k) sin(kx), sigma1 = rho0 = 1
+    ph = np.exp(1j * k * xp[0])
+    xs, us, ws = [], [], []
+    for sgn in (1.0, -1.0):
+        vs = sgn * v0
+        dv = 1j * (-1.0) * eigen_chi * Ehat / (g0 ** 3 * (om - k * vs))
+        dn = k * dv / (om - k * vs)
+        vx = vs + np.real(dv * ph)
+        u = np.zeros((3, m))
+        u[0] = vx / np.sqrt(1.0 - vx * vx)
+        xs.append(xp)
+        us.append(u)
+        ws.append(1.0 + np.real(dn * ph))
+    N = 2 * m
+    w = np.concatenate(ws) * (float(np.prod(L)) / N)
+    return dict(name=f"two_stream_3d_{n}cubed_{pairs}pairs", dim=3, n=ns, L=L, x0=x0,
+                species=[(-1.0, 1.0)], rho_bg=1.0, dt=dt, tol=tol, steps=steps,
+                x=np.concatenate(xs, axis=1), u=np.concatenate(us, axis=1), w=w,
+                sp=np.zeros(N, np.int32), A=None, U=None)
+
+
+def weibel_3d(n=32, pairs=25, v0=0.9, B0=1e-4, dt=0.04, tol=1e-11, steps=2500, *,
+              eigen_rate, eigen_chi):
+    """3D3V cold relativistic Weibel/filamentation of Sec. 5.2 (WBI, Table 1):
+    [-pi, pi]^3, pairs of electrons at +-v0 along x, seeded with the growing
+    eigenmode of Eqs. weibel-initial-fields and weibel-initial-particles
+    (k_y = 1): A_x = (B0/k) cos(k y), U_x = Gamma_W A_x, and per beam
+    v_x = s v0 + chi B0 cos(k y) / (k g0^3), v_y = s chi v0 B0 sin(k y) / (g0 Gamma_W),
+    w = 1 - s chi v0 k B0 cos(k y) / (g0 Gamma_W^2).  eigen_rate (Gamma_W) and
+    eigen_chi are inputs, not computed here."""
+    L = [2.0 * math.pi] * 3
+    x0 = [-math.pi] * 3
+    ns = [n, n, n]
+    k = 2.0 * math.pi / L[1]
+    xp = _quiet_pairs_3d(ns, L, x0, pairs)
+    m = xp.shape[1]
+    g0 = 1.0 / math.sqrt(1.0 - v0 * v0)
+    G = eigen_rate
+    y = xp[1]
+    xs, us, ws = [], [], []
+    for sgn in (1.0, -1.0):
+        vx = sgn * v0 + eigen_chi * B0 * np.cos(k * y) / (k * g0 ** 3)
+        vy = sgn * eigen_chi * v0 * B0 * np.sin(k * y) / (g0 * G)
+        gam = 1.0 / np.sqrt(1.0 - vx * vx - vy * vy)
+        u = np.zeros((3, m))
+        u[0] = gam * vx
+        u[1] = gam * vy
+        xs.append(xp)
+        us.append(u)
+        ws.append(1.0 - sgn * eigen_chi * v0 * k * B0 * np.cos(k * y) / (g0 * G * G))
+    N = 2 * m
+    w = np.concatenate(ws) * (float(np.prod(L)) / N)
+    ys = x0[1] + np.arange(n) * L[1] / n
+    Ax = np.broadcast_to((B0 / k) * np.cos(k * ys)[None, :, None], (n, n, n)).reshape(-1)
+    A = np.zeros((3, n ** 3))
+    U = np.zeros((3, n ** 3))
+    A[0] = Ax
+    U[0] = G * Ax
+    return dict(name=f"weibel_3d_{n}cubed_{pairs}pairs", dim=3, n=ns, L=L, x0=x0,
+                species=[(-1.0, 1.0)], rho_bg=1.0, dt=dt, tol=tol, steps=steps,
+                x=np.concatenate(xs, axis=1), u=np.concatenate(us, axis=1), w=w,
+                sp=np.zeros(N, np.int32), A=A, U=U)
+
+
 def random_fields(rng, Ng, scale=1e-2):
     """Smooth-free random mesh data for unit-level parity checks."""
     return scale * rng.standard_normal((3, Ng))

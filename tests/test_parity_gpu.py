@@ -62,8 +62,13 @@ def _two_species_2d():
     return cfg
 
 
+def _thermal_3d():
+    return pic_inputs.thermal_box(dim=3, n=8, ppc=2, T=0.05, u_drift=0.3, dt=0.2, seed=4)
+
+
 CASES = {
     "1d_two_stream": small_1d,
+    "3d_thermal": _thermal_3d,
     "2d_weibel": small_2d,
     "2d_ragged_knots": _ragged_2d,
     "2d_fast_multicross": _fast_2d,
@@ -163,6 +168,31 @@ def test_cell_sort_does_not_change_results():
     assert rel_err(Pa, Pb) < 1e-9
     assert np.array_equal(wa, wb) and np.array_equal(sa, sb)
     _field_close(a.fields(), b.fields(), 1e-9, cfg)
+
+
+def test_inner_warm_start_option():
+    """Option inner_warm_start (later evaluations of a step start the inner
+    iteration from the previous evaluation's orbit velocity), used with an
+    inner tolerance ten times tighter: the steps still converge to the same
+    fixed point as the cold-started oracle, with fewer inner iterations."""
+    cfg = small_2d()
+    o = make_oracle(cfg)
+    o.start()
+    s = make_gpu(cfg, inner_warm_start=1, inner_tol_scale=0.1)
+    s.start()
+    c = make_gpu(cfg)
+    c.start()
+    for _ in range(3):
+        ro = o.step(1e-12)
+        rs = s.step(1e-12)
+        rc = c.step(1e-12)
+        assert ro["status"] == 0 and rs["status"] == 0 and rc["status"] == 0
+        assert abs(rs["rel_dE"]) < 1e-11
+    assert s.stats()["inner_iters"] < c.stats()["inner_iters"]
+    xs, Ps, _, _ = s.particles()
+    xo, Po, _, _ = o.particles()
+    assert np.abs(periodic_diff(xs, xo, cfg["L"])).max() < 1e-9 * max(cfg["L"])
+    assert rel_err(Ps, Po) < 1e-9
 
 
 def test_failed_step_leaves_state_unchanged():
