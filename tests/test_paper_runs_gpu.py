@@ -8,9 +8,14 @@ amplitude |f_k| / N_g must match the closed-form finite-grid rates
 Gamma_TS = 9.109138040e-2 and Gamma_W = 5.103647904e-1 (the paper's own fits
 are off by 7.95e-4 and 1.07e-3), and the total energy must be conserved to
 the nonlinear tolerance (Thm. energy; the paper reports <= 3.7e-12 and
-3.5e-12 over much longer runs).
+3.5e-12 over much longer runs).  The two-stream fit also reproduces the rate
+the paper prints for TSI-0.1, 0.09101901, to all eight printed digits.  The
+Weibel fit lands closer to Gamma_W than the paper's printed 0.510911239; the
+paper does not state its loading in enough detail (positions of the 25 pairs
+in a cell) to reproduce that number.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -19,6 +24,14 @@ import pic_inputs
 from tests._common import make_gpu
 
 pytestmark = pytest.mark.gpu
+
+
+def _golden(name):
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+    for line in open(path):
+        if line.startswith(name + " "):
+            return float(line.split()[1])
+    raise KeyError(name)
 
 
 def _spectral_deriv(f, axis, L):
@@ -61,6 +74,8 @@ def test_tsi_3d_growth_rate_and_energy():
     print(f"TSI-0.1 3D: fitted rate {rate:.8f} vs Gamma_TS {G:.8f} (rel {rate / G - 1:+.2e}), "
           f"max |dE/E| {dE:.2e}, stats {s.stats()}")
     assert rate == pytest.approx(G, rel=3e-3)
+    # the same fit reproduces the rate the paper prints for TSI-0.1 (8 digits)
+    assert rate == pytest.approx(_golden("tsi01_fitted_rate"), abs=2e-8)
     assert dE < 1e-11
 
 
