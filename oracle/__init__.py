@@ -48,6 +48,7 @@ class _Params(C.Structure):
         ("beta", C.c_double), ("lambda_", C.c_double), ("decrease_coef", C.c_double),
         ("growth_limit", C.c_double), ("tol_abs_ratio", C.c_double), ("inner_tol_scale", C.c_double),
         ("nspecies", C.c_int), ("q", C.c_double * 4), ("m", C.c_double * 4),
+        ("order", C.c_int), ("refine_max", C.c_int),
     ]
 
 
@@ -84,6 +85,12 @@ def lib():
         L.orc_eval_map.argtypes = [C.c_void_p, _D, C.c_double, _D, _D, _D, _I]
         L.orc_num_particles.restype = C.c_long
         L.orc_num_particles.argtypes = [C.c_void_p]
+        L.orc_last_refined.restype = C.c_long
+        L.orc_last_refined.argtypes = [C.c_void_p]
+        L.orc_S1.restype = C.c_double
+        L.orc_S1.argtypes = [C.c_double]
+        L.orc_dS1.restype = C.c_double
+        L.orc_dS1.argtypes = [C.c_double]
         L.orc_get_particles.argtypes = [C.c_void_p, _D, _D, _D, _I]
         L.orc_get_fields.argtypes = [C.c_void_p, _D, _D, _D, _D, _D, _D]
         L.orc_set_fields.argtypes = [C.c_void_p, _D, _D, _D, _D, _D, _D]
@@ -131,7 +138,7 @@ def _f64(a):
 DEFAULTS = dict(dt=0.1, kappa=1.0, sigma1=1.0, sigma2=1.0, rho_bg=0.0, project=1, gl_points=8,
                 inner_max=64, outer_max=80, anderson_m=4, anderson_start=2, backtrack_levels=7,
                 beta=0.5, lambda_=1e-12, decrease_coef=1e-4, growth_limit=1.2,
-                tol_abs_ratio=0.01, inner_tol_scale=1.0)
+                tol_abs_ratio=0.01, inner_tol_scale=1.0, order=2, refine_max=0)
 
 
 def S2(xi: float) -> float:
@@ -140,6 +147,14 @@ def S2(xi: float) -> float:
 
 def dS2(xi: float) -> float:
     return lib().orc_dS2(float(xi))
+
+
+def S1(xi: float) -> float:
+    return lib().orc_S1(float(xi))
+
+
+def dS1(xi: float) -> float:
+    return lib().orc_dS1(float(xi))
 
 
 def gauss_legendre(n: int):
@@ -258,6 +273,10 @@ class Oracle:
     # -- state access -------------------------------------------------------
     def num_particles(self) -> int:
         return int(lib().orc_num_particles(self._h))
+
+    def refined(self) -> int:
+        """Particles that needed substeps in the last map evaluation."""
+        return int(lib().orc_last_refined(self._h))
 
     def particles(self):
         npart = self.num_particles()

@@ -26,7 +26,14 @@
  *   R9 tau_rel = tol, tau_abs = tol * tol_abs_ratio;
  *   R10 phi^0 and psi^0 come from the Gauss and Lorenz constraints;
  *   R11 the first trial current is the projected point deposit of q v S(x);
- *   R12 particle charge and mass are weight times the species values.
+ *   R12 particle charge and mass are weight times the species values;
+ *   R15 degree-one shapes (Sec. 5.3 comparison) have their knots on the nodes;
+ *   R16 convergence-triggered refinement (Sec. 5.3): a particle whose solve
+ *       fails is retried with 2, 4, .. equal substeps of the field step; a
+ *       substep over [s_a, s_b] of the step sees A(s) = (1 - s) A^n + s A^{n+1}
+ *       (the time-linear potential of Eq. A-g-s) and the step's grad phi^{1/2},
+ *       starts its Picard iteration from v(p) at its own start, and deposits
+ *       its orbit current with weight (s_b - s_a) (orbit-averaged current).
  */
 #include "pic_oracle.h"
 
@@ -40,6 +47,7 @@
 
 #define WMAX 12   /* widest node window per dimension of one orbit */
 #define GLMAX 32
+#define REFMAX 3  /* largest refinement level: 2^3 substeps */
 
 typedef struct {
   orc_params p;
@@ -56,6 +64,8 @@ typedef struct {
   /* step work */
   double *vbar, *v0, *Am, *pn, *Pnew;
   int *iters;
+  int *nsub;        /* substeps of each particle's accepted solve (R16) */
+  long refined;     /* particles that needed substeps in the last evaluation */
   double gl_t[GLMAX], gl_w[GLMAX];
   double E0;
   int started;
@@ -77,6 +87,16 @@ double orc_dS2(double xi) {
   double a = fabs(xi);
   double sg = (xi > 0.0) ? 1.0 : ((xi < 0.0) ? -1.0 : 0.0);
   return sg * (-pos(1.5 - a) + 3.0 * pos(0.5 - a));
+}
+
+/* linear B-spline S_1(xi) = (1 - |xi|)_+ (Sec. 5.3, degree r = 1) */
+double orc_S1(double xi) { return pos(1.0 - fabs(xi)); }
+
+/* derivative of S_1 with respect to xi (one-sided values at its knots are
+   never needed: quadrature points lie inside knot-split pieces) */
+double orc_dS1(double xi) {
+  if (fabs(xi) >= 1.0) return 0.0;
+  return xi > 0.0 ? -1.0 : (xi < 0.0 ? 1.0 : 0.0);
 }
 
 /* ------------------------------------------------------------------ */
@@ -401,6 +421,15 @@ int orc_field_solve(void *h, const double *j, double *gradphi_half, double *A_np
   return 0;
 }
 
+/* the particle shape of degree o->p.order, its derivative, the half-width
+   of its support and the offset of its knots from the nodes (R1, R15) */
+static double shp(const orc *o, double xi) { return o->p.order == 1 ? orc_S1(xi) : orc_S2(xi); }
+static double dshp(const orc *o, double xi) {
+  return o->p.order == 1 ? orc_dS1(xi) : orc_dS2(xi);
+}
+static double shp_rad(const orc *o) { return o->p.order == 1 ? 1.0 : 1.5; }
+static double knot_off(const orc *o) { return o->p.order == 1 ? 0.0 : 0.5; }
+
 /* ------------------------------------------------------------------ */
 /* point interpolant A_h(x) = sum_g A_g S_g(x), Eq. mesh-interpolant   */
 /* ------------------------------------------------------------------ */
@@ -412,9 +441,10 @@ static void node_coord(const orc *o, const double *xp, double *u) {
 static void interp_point(const orc *o, const double *u, const double *F, int ncomp,
                          double *out) {
   int d = o->p.dim, lo[3] = {0, 0, 0}, wn[3] = {1, 1, 1};
+  const double rad = shp_rad(o);
   for (int l = 0; l < d; l++) {
-    lo[l] = (int)floor(u[l] - 1.5);
-    wn[l] = (int)ceil(u[l] + 1.5) - lo[l] + 1;
+    lo[l] = (int)floor(u[l] - rad);
+    wn[l] = (int)ceil(u[l] + rad) - lo[l] + 1;
   }
   for (int c = 0; c < ncomp; c++) out[c] = 0.0;
   for (int c2 = 0; c2 < wn[2]; c2++)
@@ -424,7 +454,7 @@ static void interp_point(const orc *o, const double *u, const double *F, int nco
         double S = 1.0;
         int gi[3] = {0, 0, 0};
         for (int l = 0; l < d; l++) {
-          S *= orc_S2(u[l] - (lo[l] + cc[l]));
+          S *= shp(o, u[l] - (lo[l] + cc[l]));
           gi[l] = mod(lo[l] + cc[l], o->p.n[l]);
         }
         if (S == 0.0) continue;
@@ -443,21 +473,25 @@ typedef struct {
   double Sbar[WMAX * WMAX * WMAX];
 } orbit_t;
 
-static int orbit_eval(const orc *o, const double *xp, const double *vb,
+/* The orbit x(s) = x + s dt_orb vbar, s in [0, 1], over a particle time
+   step dt_orb (the field step, or a substep of it, R16); An and Anp1 are the
+   potentials at the start and end of that time interval. */
+static int orbit_eval(const orc *o, const double *xp, const double *vb, double dt_orb,
                       const double *gradphi, const double *An, const double *Anp1,
                       const double *Uhalf, orbit_t *ob, int want_sbar) {
   int d = o->p.dim, Ng = o->Ng;
   double u0[3], del[3];
+  const double rad = shp_rad(o), ko = knot_off(o);
   node_coord(o, xp, u0);
   for (int l = 0; l < 3; l++) {
-    del[l] = (l < d) ? o->p.dt * vb[l] / o->dx[l] : 0.0;
+    del[l] = (l < d) ? dt_orb * vb[l] / o->dx[l] : 0.0;
     ob->lo[l] = 0;
     ob->wn[l] = 1;
   }
   for (int l = 0; l < d; l++) {
     double a = fmin(u0[l], u0[l] + del[l]), b = fmax(u0[l], u0[l] + del[l]);
-    ob->lo[l] = (int)floor(a - 1.5);
-    ob->wn[l] = (int)ceil(b + 1.5) - ob->lo[l] + 1;
+    ob->lo[l] = (int)floor(a - rad);
+    ob->wn[l] = (int)ceil(b + rad) - ob->lo[l] + 1;
     if (ob->wn[l] > WMAX) return -1;
   }
   /* knots crossed by the unwrapped straight orbit, Eq. rel-orbit */
@@ -468,7 +502,7 @@ static int orbit_eval(const orc *o, const double *xp, const double *vb,
   for (int l = 0; l < d; l++) {
     if (del[l] == 0.0) continue;
     double a = fmin(u0[l], u0[l] + del[l]), b = fmax(u0[l], u0[l] + del[l]);
-    for (double hk = floor(a - 0.5) + 1.5; hk < b; hk += 1.0) {
+    for (double hk = floor(a - ko) + 1.0 + ko; hk < b; hk += 1.0) {
       if (hk <= a) continue;
       bs[nb++] = (hk - u0[l]) / del[l];
     }
@@ -493,8 +527,8 @@ static int orbit_eval(const orc *o, const double *xp, const double *vb,
         for (int c = 0; c < ob->wn[l]; c++) {
           if (l < d) {
             double xi = u0[l] + s * del[l] - (ob->lo[l] + c);
-            sv[l][c] = orc_S2(xi);
-            dv[l][c] = orc_dS2(xi) / o->dx[l];
+            sv[l][c] = shp(o, xi);
+            dv[l][c] = dshp(o, xi) / o->dx[l];
           } else {
             sv[l][c] = 1.0;
             dv[l][c] = 0.0;
@@ -609,7 +643,8 @@ void orc_push(const double *Pn, const double *Am, const double *Ap, const double
 /* ------------------------------------------------------------------ */
 void *orc_create(const orc_params *prm) {
   if (!prm || prm->dim < 1 || prm->dim > 3 || prm->nspecies < 1 ||
-      prm->nspecies > ORC_MAX_SPECIES || prm->gl_points < 1 || prm->gl_points > GLMAX)
+      prm->nspecies > ORC_MAX_SPECIES || prm->gl_points < 1 || prm->gl_points > GLMAX ||
+      (prm->order != 1 && prm->order != 2) || prm->refine_max < 0 || prm->refine_max > REFMAX)
     return NULL;
   orc *o = (orc *)calloc(1, sizeof(orc));
   o->p = *prm;
@@ -634,6 +669,7 @@ void *orc_create(const orc_params *prm) {
 static void free_particles(orc *o) {
   free(o->sp); free(o->x); free(o->P); free(o->w); free(o->u_mech);
   free(o->vbar); free(o->v0); free(o->Am); free(o->pn); free(o->Pnew); free(o->iters);
+  free(o->nsub);
   o->sp = NULL; o->x = o->P = o->w = o->u_mech = NULL;
   o->vbar = o->v0 = o->Am = o->pn = o->Pnew = NULL; o->iters = NULL;
 }
@@ -647,6 +683,8 @@ void orc_free(void *h) {
 }
 
 long orc_num_particles(void *h) { return ((orc *)h)->np; }
+
+long orc_last_refined(void *h) { return ((orc *)h)->refined; }
 
 static double wrap_pos(const orc *o, int l, double x) {
   double r = fmod(x - o->p.x0[l], o->p.L[l]);
@@ -672,6 +710,7 @@ int orc_set_particles(void *h, long np, const int *species, const double *x,
   o->pn = (double *)calloc(3 * (n ? n : 1), sizeof(double));
   o->Pnew = (double *)calloc(3 * (n ? n : 1), sizeof(double));
   o->iters = (int *)calloc(n ? n : 1, sizeof(int));
+  o->nsub = (int *)calloc(n ? n : 1, sizeof(int));
   for (size_t i = 0; i < n; i++) {
     o->sp[i] = species ? species[i] : 0;
     if (o->sp[i] < 0 || o->sp[i] >= o->p.nspecies) return ORC_EARG;
@@ -776,8 +815,8 @@ static void point_deposit(orc *o, double *rho, double *J) {
     for (int c = 0; c < 3; c++) v[c] = p[c] / (m * gam);
     int lo[3] = {0, 0, 0}, wn[3] = {1, 1, 1};
     for (int l = 0; l < d; l++) {
-      lo[l] = (int)floor(u[l] - 1.5);
-      wn[l] = (int)ceil(u[l] + 1.5) - lo[l] + 1;
+      lo[l] = (int)floor(u[l] - shp_rad(o));
+      wn[l] = (int)ceil(u[l] + shp_rad(o)) - lo[l] + 1;
     }
     for (int c2 = 0; c2 < wn[2]; c2++)
       for (int c1 = 0; c1 < wn[1]; c1++)
@@ -785,7 +824,7 @@ static void point_deposit(orc *o, double *rho, double *J) {
           int cc[3] = {c0, c1, c2}, gi[3] = {0, 0, 0};
           double S = 1.0;
           for (int l = 0; l < d; l++) {
-            S *= orc_S2(u[l] - (lo[l] + cc[l]));
+            S *= shp(o, u[l] - (lo[l] + cc[l]));
             gi[l] = mod(lo[l] + cc[l], o->p.n[l]);
           }
           size_t g = (size_t)gi[0] + (size_t)o->p.n[0] * (gi[1] + (size_t)o->p.n[1] * gi[2]);
@@ -895,6 +934,126 @@ static void step_start(orc *o) {
   }
 }
 
+/* ------------------------------------------------------------------ */
+/* one particle's inner solve (Sec. 4.5) with convergence-triggered    */
+/* refinement (Sec. 5.3, reading R16)                                  */
+/* ------------------------------------------------------------------ */
+
+/* time levels s_k = k / 2^R of the field step and the mesh potentials
+   A(s_k) = (1 - s_k) A^n + s_k A^{n+1} there (Eq. A-g-s) */
+typedef struct {
+  int R, nlev;
+  const double *A[(1 << REFMAX) + 1];
+  double *own[(1 << REFMAX) + 1];
+} tlev_t;
+
+static void tlev_make(const orc *o, const double *An, const double *A1, tlev_t *t) {
+  int R = o->p.refine_max < 0 ? 0 : (o->p.refine_max > REFMAX ? REFMAX : o->p.refine_max);
+  size_t N3 = (size_t)3 * o->Ng;
+  t->R = R;
+  t->nlev = (1 << R) + 1;
+  for (int k = 0; k < t->nlev; k++) {
+    t->own[k] = NULL;
+    if (k == 0) { t->A[k] = An; continue; }
+    if (k == t->nlev - 1) { t->A[k] = A1; continue; }
+    double sk = (double)k / (double)(1 << R);
+    double *a = (double *)malloc(sizeof(double) * N3);
+    for (size_t q = 0; q < N3; q++) a[q] = (1.0 - sk) * An[q] + sk * A1[q];
+    t->own[k] = a;
+    t->A[k] = a;
+  }
+}
+
+static void tlev_free(tlev_t *t) {
+  for (int k = 0; k < t->nlev; k++) free(t->own[k]);
+}
+
+typedef struct {
+  int nsub, stride;                 /* substeps of the accepted level, level-table stride */
+  double xs[1 << REFMAX][3];        /* start position of each substep */
+  double vb[1 << REFMAX][3];        /* converged orbit velocity of each substep */
+  double Pnew[3], vbar[3];          /* P^{n+1}; orbit velocity averaged over the substeps */
+  int iters;                        /* Picard iterations of the accepted level */
+} psolve_t;
+
+/* Level 0 is one particle step over the whole field step.  If any Picard
+   iteration fails (limit, non-finite or superluminal velocity, orbit wider
+   than the node window), level L retries with 2^L equal substeps, each
+   converged in turn from the previous substep's end state.  Returns 1 on
+   success; on failure ps holds the last iterate of level 0. */
+static int solve_particle(const orc *o, long i, const double *gradphi, const tlev_t *tl,
+                          double tau_r, double tau_a, psolve_t *ps) {
+  size_t n = (size_t)o->np;
+  double q = pq(o, i), m = pm(o, i), kap = o->p.kappa;
+  double x0[3], P0[3];
+  particle_x(o, i, x0);
+  for (int c = 0; c < 3; c++) P0[c] = o->P[c * n + i];
+  for (int lvl = 0; lvl <= tl->R; lvl++) {
+    int nsub = 1 << lvl, stride = 1 << (tl->R - lvl);
+    double dtau = o->p.dt / nsub;
+    double x[3] = {x0[0], x0[1], x0[2]}, P[3] = {P0[0], P0[1], P0[2]};
+    int ok = 1, its = 0;
+    for (int sub = 0; sub < nsub && ok; sub++) {
+      const double *Aa = tl->A[sub * stride], *Ab = tl->A[(sub + 1) * stride];
+      double u[3], Am[3], p[3], vb[3], Pk[3];
+      node_coord(o, x, u);
+      interp_point(o, u, Aa, 3, Am);
+      for (int c = 0; c < 3; c++) p[c] = P[c] - q * Am[c];
+      double gam = sqrt(1.0 + dot3(p, p) / (m * m * kap * kap));
+      for (int c = 0; c < 3; c++) {
+        vb[c] = p[c] / (m * gam); /* reading R5 */
+        Pk[c] = P[c];
+      }
+      int conv = 0;
+      orbit_t ob;
+      for (int it = 1; it <= o->p.inner_max; it++) {
+        its++;
+        if (orbit_eval(o, x, vb, dtau, gradphi, Aa, Ab, NULL, &ob, 0)) break;
+        double pmn[3], ppl[3], Pn1[3], vn[3];
+        orc_push(P, Am, ob.Aplus, ob.gphi, ob.D, vb, q, m, kap, dtau, pmn, ppl, Pn1, vn);
+        double diff = 0.0, nrm = 0.0;
+        int finite = 1;
+        for (int c = 0; c < 3; c++) {
+          if (!isfinite(vn[c])) finite = 0;
+          diff = fmax(diff, fabs(vn[c] - vb[c]));
+          nrm = fmax(nrm, fabs(vn[c]));
+        }
+        if (!finite || sqrt(dot3(vn, vn)) >= kap) break;
+        for (int c = 0; c < 3; c++) {
+          vb[c] = vn[c];
+          Pk[c] = Pn1[c];
+        }
+        if (diff <= tau_a + tau_r * nrm) { conv = 1; break; }
+      }
+      if (lvl == 0) { /* report the level-0 iterate if every level fails */
+        for (int c = 0; c < 3; c++) { ps->vbar[c] = vb[c]; ps->Pnew[c] = Pk[c]; }
+      }
+      if (!conv) { ok = 0; break; }
+      for (int c = 0; c < 3; c++) {
+        ps->xs[sub][c] = x[c];
+        ps->vb[sub][c] = vb[c];
+      }
+      for (int l = 0; l < o->p.dim; l++) x[l] += dtau * vb[l];
+      for (int c = 0; c < 3; c++) P[c] = Pk[c];
+    }
+    if (ok) {
+      ps->nsub = nsub;
+      ps->stride = stride;
+      ps->iters = its;
+      for (int c = 0; c < 3; c++) {
+        double v = 0.0;
+        for (int sub = 0; sub < nsub; sub++) v += ps->vb[sub][c];
+        ps->vbar[c] = v / nsub;
+        ps->Pnew[c] = P[c];
+      }
+      return 1;
+    }
+  }
+  ps->nsub = 0;
+  ps->iters = -1;
+  return 0;
+}
+
 /* one map evaluation at trial current j; returns 0 or ORC_EINNER */
 static int map_eval(orc *o, const double *j, double tau_r, double tau_a, eval_t *e,
                     double *H, int final_pass) {
@@ -905,42 +1064,27 @@ static int map_eval(orc *o, const double *j, double tau_r, double tau_a, eval_t 
   orc_field_solve(o, jp, e->gradphi, e->A1, e->Uh, e->phi1, e->psi1, e->U1, e->rho1);
   free(jp);
   int fail = 0;
-  double kap = o->p.kappa;
-#pragma omp parallel for schedule(dynamic, 64) reduction(| : fail)
+  long refined = 0;
+  tlev_t tl;
+  tlev_make(o, o->A, e->A1, &tl);
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : fail) reduction(+ : refined)
   for (long i = 0; i < (long)n; i++) {
-    double xp[3], vb[3], Pn[3], Am[3];
-    particle_x(o, i, xp);
+    psolve_t ps;
+    int conv = solve_particle(o, i, e->gradphi, &tl, tau_r, tau_a, &ps);
+    o->iters[i] = ps.iters;
+    o->nsub[i] = ps.nsub;
     for (int c = 0; c < 3; c++) {
-      vb[c] = o->v0[c * n + i]; /* reading R5 */
-      Pn[c] = o->P[c * n + i];
-      Am[c] = o->Am[c * n + i];
+      o->vbar[c * n + i] = ps.vbar[c];
+      o->Pnew[c * n + i] = ps.Pnew[c];
     }
-    double q = pq(o, i), m = pm(o, i);
-    int conv = 0, it;
-    orbit_t ob;
-    for (it = 1; it <= o->p.inner_max; it++) {
-      if (orbit_eval(o, xp, vb, e->gradphi, o->A, e->A1, NULL, &ob, 0)) break;
-      double pmn[3], ppl[3], Pn1[3], vn[3];
-      orc_push(Pn, Am, ob.Aplus, ob.gphi, ob.D, vb, q, m, kap, o->p.dt, pmn, ppl, Pn1, vn);
-      double diff = 0.0, nrm = 0.0;
-      int finite = 1;
-      for (int c = 0; c < 3; c++) {
-        if (!isfinite(vn[c])) finite = 0;
-        diff = fmax(diff, fabs(vn[c] - vb[c]));
-        nrm = fmax(nrm, fabs(vn[c]));
-      }
-      if (!finite || sqrt(dot3(vn, vn)) >= kap) break;
-      for (int c = 0; c < 3; c++) {
-        vb[c] = vn[c];
-        o->Pnew[c * n + i] = Pn1[c];
-      }
-      if (diff <= tau_a + tau_r * nrm) { conv = 1; break; }
-    }
-    o->iters[i] = conv ? it : -1;
-    for (int c = 0; c < 3; c++) o->vbar[c * n + i] = vb[c];
+    if (ps.nsub > 1) refined++;
     if (!conv) fail |= 1;
   }
-  if (fail) return ORC_EINNER;
+  o->refined = refined;
+  if (fail) {
+    tlev_free(&tl);
+    return ORC_EINNER;
+  }
   /* deposit with the final orbit velocity, Eq. orbit-current-energy; the
      same pass evaluates the chain-rule and work sums of Sec. 4.4 */
   int nthr = 1;
@@ -958,30 +1102,44 @@ static int map_eval(orc *o, const double *j, double tau_r, double tau_a, eval_t 
     double *Jt = part + (size_t)t * 3 * Ng;
 #pragma omp for schedule(static)
     for (long i = 0; i < (long)n; i++) {
-      double xp[3], vb[3];
-      particle_x(o, i, xp);
-      for (int c = 0; c < 3; c++) vb[c] = o->vbar[c * n + i];
-      orbit_t ob;
-      orbit_eval(o, xp, vb, e->gradphi, o->A, e->A1, e->Uh, &ob, 1);
-      double q = pq(o, i);
-      for (int c2 = 0; c2 < ob.wn[2]; c2++)
-        for (int c1 = 0; c1 < ob.wn[1]; c1++)
-          for (int c0 = 0; c0 < ob.wn[0]; c0++) {
-            int cc[3] = {c0, c1, c2}, gi[3];
-            for (int l = 0; l < 3; l++) gi[l] = mod(ob.lo[l] + cc[l], o->p.n[l]);
-            size_t g = (size_t)gi[0] + (size_t)o->p.n[0] * (gi[1] + (size_t)o->p.n[1] * gi[2]);
-            double Sb = ob.Sbar[c0 + ob.wn[0] * (c1 + ob.wn[1] * c2)];
-            for (int c = 0; c < 3; c++) Jt[c * Ng + g] += q * vb[c] * Sb / o->dV;
+      psolve_t ps;
+      if (o->nsub[i] > 1) {
+        /* refined particle: recover its substeps (deterministic re-solve) */
+        solve_particle(o, i, e->gradphi, &tl, tau_r, tau_a, &ps);
+      } else {
+        ps.nsub = 1;
+        ps.stride = 1 << tl.R;
+        particle_x(o, i, ps.xs[0]);
+        for (int c = 0; c < 3; c++) ps.vb[0][c] = o->vbar[c * n + i];
+      }
+      double q = pq(o, i), wsub = 1.0 / ps.nsub, dtau = o->p.dt / ps.nsub;
+      for (int sub = 0; sub < ps.nsub; sub++) {
+        const double *Aa = tl.A[sub * ps.stride], *Ab = tl.A[(sub + 1) * ps.stride];
+        const double *vb = ps.vb[sub];
+        orbit_t ob;
+        orbit_eval(o, ps.xs[sub], vb, dtau, e->gradphi, Aa, Ab, e->Uh, &ob, 1);
+        /* orbit-averaged current: each substep weighs its share of the step */
+        for (int c2 = 0; c2 < ob.wn[2]; c2++)
+          for (int c1 = 0; c1 < ob.wn[1]; c1++)
+            for (int c0 = 0; c0 < ob.wn[0]; c0++) {
+              int cc[3] = {c0, c1, c2}, gi[3];
+              for (int l = 0; l < 3; l++) gi[l] = mod(ob.lo[l] + cc[l], o->p.n[l]);
+              size_t g = (size_t)gi[0] + (size_t)o->p.n[0] * (gi[1] + (size_t)o->p.n[1] * gi[2]);
+              double Sb = ob.Sbar[c0 + ob.wn[0] * (c1 + ob.wn[1] * c2)];
+              for (int c = 0; c < 3; c++) Jt[c * Ng + g] += wsub * q * vb[c] * Sb / o->dV;
+            }
+        if (final_pass) {
+          double Dv[3], Am[3], u[3];
+          node_coord(o, ps.xs[sub], u);
+          interp_point(o, u, Aa, 3, Am);
+          for (int c = 0; c < 3; c++)
+            Dv[c] = ob.D[c * 3 + 0] * vb[0] + ob.D[c * 3 + 1] * vb[1] + ob.D[c * 3 + 2] * vb[2];
+          for (int c = 0; c < 3; c++) {
+            double Ebar = -ob.gphi[c] - ob.Ubar[c];
+            work += wsub * q * vb[c] * Ebar;
+            double RA = ob.Aplus[c] - Am[c] - dtau * (ob.Ubar[c] + Dv[c]);
+            chain += RA * RA;
           }
-      if (final_pass) {
-        double Dv[3];
-        for (int c = 0; c < 3; c++)
-          Dv[c] = ob.D[c * 3 + 0] * vb[0] + ob.D[c * 3 + 1] * vb[1] + ob.D[c * 3 + 2] * vb[2];
-        for (int c = 0; c < 3; c++) {
-          double Ebar = -ob.gphi[c] - ob.Ubar[c];
-          work += q * vb[c] * Ebar;
-          double RA = ob.Aplus[c] - o->Am[c * n + i] - o->p.dt * (ob.Ubar[c] + Dv[c]);
-          chain += RA * RA;
         }
       }
     }
@@ -990,6 +1148,7 @@ static int map_eval(orc *o, const double *j, double tau_r, double tau_a, eval_t 
   for (int t = 0; t < nthr; t++)
     for (size_t k = 0; k < 3 * Ng; k++) e->Jorb[k] += part[(size_t)t * 3 * Ng + k];
   free(part);
+  tlev_free(&tl);
   e->work_particles = work;
   e->chain_sq = chain;
   memcpy(H, e->Jorb, sizeof(double) * 3 * Ng);
@@ -1007,7 +1166,10 @@ int orc_deposit(void *h, const double *vbar, double *Jorb) {
     particle_x(o, (long)i, xp);
     for (int c = 0; c < 3; c++) vb[c] = vbar[c * n + i];
     orbit_t ob;
-    if (orbit_eval(o, xp, vb, NULL, zero, zero, NULL, &ob, 1)) { free(zero); return ORC_EARG; }
+    if (orbit_eval(o, xp, vb, o->p.dt, NULL, zero, zero, NULL, &ob, 1)) {
+      free(zero);
+      return ORC_EARG;
+    }
     for (int c2 = 0; c2 < ob.wn[2]; c2++)
       for (int c1 = 0; c1 < ob.wn[1]; c1++)
         for (int c0 = 0; c0 < ob.wn[0]; c0++) {
@@ -1029,7 +1191,7 @@ int orc_orbit_data(void *h, const double *x, const double *vbar, const double *g
   orbit_t ob;
   double xp[3] = {0, 0, 0};
   for (int l = 0; l < o->p.dim; l++) xp[l] = x[l];
-  if (orbit_eval(o, xp, vbar, gradphi, An, Anp1, Uhalf, &ob, 1)) return ORC_EARG;
+  if (orbit_eval(o, xp, vbar, o->p.dt, gradphi, An, Anp1, Uhalf, &ob, 1)) return ORC_EARG;
   for (int c = 0; c < 3; c++) {
     if (gphi) gphi[c] = ob.gphi[c];
     if (Ubar) Ubar[c] = ob.Ubar[c];
@@ -1293,7 +1455,7 @@ int orc_step(void *h, double tol, orc_report *rep) {
 int orc_eval_particles(void *h, const double *j, double tol, long nidx, const long *idx,
                        double *vbar, double *Pnew, int *inner_counts) {
   orc *o = (orc *)h;
-  size_t n = (size_t)o->np, Ng = (size_t)o->Ng;
+  size_t Ng = (size_t)o->Ng;
   double ti = tol * o->p.inner_tol_scale, ta = ti * o->p.tol_abs_ratio;
   double *jp = (double *)malloc(sizeof(double) * 3 * Ng);
   memcpy(jp, j, sizeof(double) * 3 * Ng);
@@ -1303,45 +1465,20 @@ int orc_eval_particles(void *h, const double *j, double tol, long nidx, const lo
   orc_field_solve(o, jp, e.gradphi, e.A1, e.Uh, e.phi1, e.psi1, e.U1, e.rho1);
   free(jp);
   int fail = 0;
+  tlev_t tl;
+  tlev_make(o, o->A, e.A1, &tl);
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : fail)
   for (long k = 0; k < nidx; k++) {
-    long i = idx[k];
-    double xp[3], u[3], Am[3], vb[3], Pn[3];
-    particle_x(o, i, xp);
-    node_coord(o, xp, u);
-    interp_point(o, u, o->A, 3, Am);
-    double q = pq(o, i), m = pm(o, i), p[3];
+    psolve_t ps;
+    int conv = solve_particle(o, idx[k], e.gradphi, &tl, ti, ta, &ps);
     for (int c = 0; c < 3; c++) {
-      Pn[c] = o->P[c * n + i];
-      p[c] = Pn[c] - q * Am[c];
+      vbar[c * nidx + k] = ps.vbar[c];
+      Pnew[c * nidx + k] = ps.Pnew[c];
     }
-    double gam = sqrt(1.0 + dot3(p, p) / (m * m * o->p.kappa * o->p.kappa));
-    for (int c = 0; c < 3; c++) vb[c] = p[c] / (m * gam);
-    int conv = 0, it;
-    double Pk[3] = {Pn[0], Pn[1], Pn[2]};
-    orbit_t ob;
-    for (it = 1; it <= o->p.inner_max; it++) {
-      if (orbit_eval(o, xp, vb, e.gradphi, o->A, e.A1, NULL, &ob, 0)) break;
-      double pmn[3], ppl[3], Pn1[3], vn[3];
-      orc_push(Pn, Am, ob.Aplus, ob.gphi, ob.D, vb, q, m, o->p.kappa, o->p.dt, pmn, ppl, Pn1, vn);
-      double diff = 0.0, nrm = 0.0;
-      int finite = 1;
-      for (int c = 0; c < 3; c++) {
-        if (!isfinite(vn[c])) finite = 0;
-        diff = fmax(diff, fabs(vn[c] - vb[c]));
-        nrm = fmax(nrm, fabs(vn[c]));
-      }
-      if (!finite || sqrt(dot3(vn, vn)) >= o->p.kappa) break;
-      for (int c = 0; c < 3; c++) { vb[c] = vn[c]; Pk[c] = Pn1[c]; }
-      if (diff <= ta + ti * nrm) { conv = 1; break; }
-    }
-    for (int c = 0; c < 3; c++) {
-      vbar[c * nidx + k] = vb[c];
-      Pnew[c * nidx + k] = Pk[c];
-    }
-    inner_counts[k] = conv ? it : -1;
+    inner_counts[k] = ps.iters;
     if (!conv) fail |= 1;
   }
+  tlev_free(&tl);
   eval_free(&e);
   return fail ? ORC_EINNER : ORC_OK;
 }

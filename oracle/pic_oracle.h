@@ -41,6 +41,11 @@ typedef struct {
   double beta, lambda, decrease_coef, growth_limit, tol_abs_ratio, inner_tol_scale;
   int nspecies;
   double q[ORC_MAX_SPECIES], m[ORC_MAX_SPECIES]; /* per unit weight */
+  int order;          /* B-spline degree r of the particle shape: 2 (paper's
+                         production runs) or 1 (Sec. 5.3 comparison) */
+  int refine_max;     /* convergence-triggered particle refinement (Sec. 5.3):
+                         a particle whose solve fails is retried with 2, 4, ..
+                         2^refine_max equal substeps; 0 = off */
 } orc_params;
 
 typedef struct {
@@ -68,6 +73,8 @@ int orc_step(void *h, double tol, orc_report *rep);
 int orc_eval_map(void *h, const double *j, double tol, double *H, double *vbar,
                  double *Pnew, int *inner_counts);
 long orc_num_particles(void *h);
+/* particles that needed substeps (refinement) in the last map evaluation */
+long orc_last_refined(void *h);
 int orc_get_particles(void *h, double *x, double *P, double *w, int *species);
 int orc_get_fields(void *h, double *phi, double *psi, double *A, double *U,
                    double *rho, double *J);
@@ -77,6 +84,8 @@ int orc_set_fields(void *h, const double *phi, const double *psi, const double *
 /* unit-level pieces, exposed so that tests can pin them one by one */
 double orc_S2(double xi);
 double orc_dS2(double xi);
+double orc_S1(double xi);
+double orc_dS1(double xi);
 void orc_gauss_legendre(int n, double *nodes, double *weights);
 void orc_dft(int dim, const int *n, const double *in_re, const double *in_im,
              double *out_re, double *out_im, int inverse);
