@@ -13,6 +13,12 @@ T = 0.01, dt = 0.05, tolerance 1e-10; FP64 path (value) and FP32-mixed path
 (reported beside it).  Inputs are generated once (seeded), resident in HBM
 before the timed region; L2 is flushed between timed steps.
 
+The line also carries the batched ensemble ("ensemble"): 256 independent 1D3V
+two-stream instances of uneven sizes advanced by one pic_batch (FP32-mixed and
+FP64), against the plain FP64 path (one context per instance, stepped in turn),
+and the large case ("large"): 512^2 Weibel with mobile ions, 67,108,864
+particles, FP32-mixed, cell sort every 10 steps.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 from __future__ import annotations
@@ -133,16 +139,22 @@ def algorithmic_bytes(dim, rsize, pushes):
 
 # DRAM bytes per launch of the particle-map kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of two launches) from ncu captures of the kernel
-# source whose SHA-256 starts with the key (profiles/k_map_traffic_*.md); the
-# roofline reports null traffic once particle.cu has changed since.
+# sources whose hash (kernel_source_hash) is the key (profiles/k_map_traffic_*.md);
+# the roofline reports null traffic once those sources have changed since.
 KNOWN_TRAFFIC = {"838c7972769b2667": {"fp64": 140.94e6, "mixed": 73.46e6}}
 
 
-def measured_traffic(label):
+def kernel_source_hash():
+    """SHA-256 (first 16 hex digits) of the particle-map kernel sources."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2609_36383_b300", "csrc", "particle.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return KNOWN_TRAFFIC.get(h, {}).get(label)
+    h = hashlib.sha256()
+    for f in ("map_device.cuh", "particle.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2609_36383_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(label):
+    return KNOWN_TRAFFIC.get(kernel_source_hash(), {}).get(label)
 
 
 # ---------------------------------------------------------------- rank aggregation
@@ -157,6 +169,130 @@ def aggregate(dist, pushes, ms, device="cpu"):
     m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
     dist.all_reduce(m, op=dist.ReduceOp.MAX)
     return float(t.item()) / (float(m.item()) * 1e-3), float(m.item())
+
+
+# ---------------------------------------------------------------- ensemble
+ENSEMBLE = "two_stream_ensemble_256x1d"
+
+
+def run_ensemble(args, rank, barrier, flush, stream):
+    """The batched ensemble: 256 independent 1D3V two-stream instances (mesh
+    sizes 32..512, 16..256 particles per cell, beam u 0.2..0.95, own seeds)
+    advanced by one pic_batch, FP32-mixed (the ensemble's configuration) and
+    FP64, against the plain FP64 path: one single-problem context per
+    instance, stepped one after the other."""
+    import torch
+
+    import paper_2609_36383_b300 as P
+    import pic_inputs
+    cfgs = pic_inputs.two_stream_ensemble(B=256, seed=rank)
+    tol = cfgs[0]["tol"]
+    nps = [c["w"].shape[0] for c in cfgs]
+
+    def timed(step_fn, nsteps):
+        ms, pushes, drift, evals = 0.0, 0, 0.0, []
+        for _ in range(nsteps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reps = step_fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            for n, r in zip(nps, reps):
+                if r["status"] != 0:
+                    raise RuntimeError(f"ensemble step failed: {r}")
+                pushes += n * r["map_evals"]
+                drift = max(drift, abs(r["rel_dE"]))
+                evals.append(r["map_evals"])
+        return ms, pushes, drift, evals
+
+    out = {}
+    for label, prec in (("mixed", P.PIC_MIXED), ("fp64", P.PIC_FP64)):
+        bt = P.batch_from_configs(cfgs, precision=prec, sort_every=10)
+        bt.start()
+        for _ in range(args.warmup):
+            bt.step(tol)
+        bt.reset_stats()
+        barrier()
+        ms, pushes, drift, evals = timed(lambda: bt.step(tol), args.steps)
+        barrier()
+        st = bt.stats()
+        bt.close()
+        out[label] = dict(ms=ms, pushes=pushes, drift=drift, evals=evals, stats=st)
+    if args.only != "ensemble":
+        # the plain FP64 path: one context per instance, stepped in turn
+        sims = [P.from_config(c, precision=P.PIC_FP64) for c in cfgs]
+        for s in sims:
+            s.start()
+        for _ in range(args.warmup):
+            for s in sims:
+                s.step(tol, raise_on_fail=True)
+        barrier()
+        ms, pushes, drift, evals = timed(lambda: [s.step(tol, raise_on_fail=True) for s in sims],
+                                         args.steps)
+        barrier()
+        for s in sims:
+            s.close()
+        out["single_fp64"] = dict(ms=ms, pushes=pushes, drift=drift, evals=evals)
+    return out, sum(nps)
+
+
+# ---------------------------------------------------------------- large case
+LARGE = "weibel_2d_ions_512x512_256ppc"
+
+
+def run_large(args, rank, barrier, flush, stream):
+    """The large 2D3V Weibel case with a mobile ion species: 512^2 mesh,
+    counter-streaming electrons u_z = +-0.9 with T = 0.05 (64 + 64 per cell)
+    and ions of mass ratio 100 at rest (128 per cell), 67,108,864 particles,
+    dt = 0.02, tol 1e-10, FP32-mixed, cell sort every 10 steps."""
+    import torch
+
+    import paper_2609_36383_b300 as P
+    import pic_inputs
+    cfg = pic_inputs.weibel_2d_ions(seed=rank)
+    npart = cfg["w"].shape[0]
+    sim = P.from_config(cfg, precision=P.PIC_MIXED, sort_every=10)
+    del cfg["x"], cfg["u"], cfg["w"], cfg["sp"]
+    sim.start()
+    for _ in range(args.warmup):
+        sim.step(cfg["tol"], raise_on_fail=True)
+    sim.reset_stats()
+    barrier()
+    ms, pushes, drift, evals = 0.0, 0, 0.0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = sim.step(cfg["tol"], raise_on_fail=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        pushes += npart * r["map_evals"]
+        drift = max(drift, abs(r["rel_dE"]))
+        evals.append(r["map_evals"])
+    barrier()
+    st = sim.stats()
+    sim.close()
+    return dict(ms=ms, pushes=pushes, drift=drift, evals=evals, stats=st, particles=npart)
+
+
+def large_summary(dist, lg, steps, peak32):
+    v, t = aggregate(dist, lg["pushes"], lg["ms"], "cuda")
+    st = lg["stats"]
+    avg = st["map_ms"] / max(st["map_launches"], 1)
+    ach = algorithmic_flops(2, st) / max(st["map_launches"], 1) / (avg * 1e-3)
+    return {"workload": LARGE, "particles": lg["particles"], "value": v, "unit": UNIT,
+            "dtype": "f32-mixed", "ms_per_step": t / steps, "max_abs_rel_dE": lg["drift"],
+            "mean_map_evals_per_step": statistics.mean(lg["evals"]),
+            "mean_inner_iters": st["inner_iters"] / max(st["pushes"], 1),
+            "sort_every": 10, "l2": "inputs (about 7 GB of particle state) exceed L2",
+            "map_kernel": {"share_of_step": st["map_ms"] / max(lg["ms"], 1e-9),
+                           "achieved_tflops": ach / 1e12, "peak_tflops": peak32 / 1e12,
+                           "frac": ach / peak32, "avg_ms": avg}}
 
 
 # ---------------------------------------------------------------- our arm
@@ -203,6 +339,19 @@ def run_ours(args):
             reports.append(r)
         return pushes, ms, reports
 
+    if args.only == "large":
+        lg = run_large(args, rank, barrier, flush, stream)
+        print(json.dumps({"profile_run": "large", "ms": lg["ms"], "pushes": lg["pushes"],
+                          "stats": lg["stats"]}), flush=True)
+        return
+    if args.only == "ensemble":
+        ens, ntot = run_ensemble(args, rank, barrier, flush, stream)
+        for label, r in ens.items():
+            print(json.dumps({"profile_run": f"ensemble_{label}", "ms": r["ms"],
+                              "pushes": r["pushes"], "particles": ntot,
+                              "stats": r.get("stats")}), flush=True)
+        return
+
     results = {}
     # (label, precision, options): the FP64 and FP32-mixed paths with the
     # paper's cold-started inner iteration, and the FP64 path with the
@@ -230,6 +379,11 @@ def run_ours(args):
             fp64_sim = sim
         else:
             sim.close()
+    ens = lg = None
+    if not (args.only or args.skip_e2e):
+        ens, ens_particles = run_ensemble(args, rank, barrier, flush, stream)
+        if not args.no_large:
+            lg = run_large(args, rank, barrier, flush, stream)
     clk.__exit__(None, None, None)
     clocks = clk.summary()
     if args.only or args.skip_e2e:
@@ -353,6 +507,8 @@ def run_ours(args):
                     "peak_source": hbm_src,
                     "frac": bytes_launch / (avg_ms * 1e-3) / 1e9 / hbm},
         },
+        "ensemble": ensemble_summary(dist, ens, ens_particles, args.steps),
+        "large": large_summary(dist, lg, args.steps, peak32) if lg else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": st["launches"],
@@ -364,6 +520,29 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def ensemble_summary(dist, ens, particles, steps):
+    v = {k: aggregate(dist, r["pushes"], r["ms"], "cuda")[0] for k, r in ens.items()}
+    summ = {
+        "workload": ENSEMBLE, "instances": 256, "particles": particles,
+        "note": "one pic_batch; per-instance Algorithm 1 decided on the device; rounds "
+                "replayed as one CUDA graph each; L2 flushed before every timed step",
+        "value": v["mixed"], "unit": UNIT, "dtype": "f32-mixed",
+        "ms_per_step": ens["mixed"]["ms"] / steps,
+        "max_abs_rel_dE": ens["mixed"]["drift"],
+        "mean_map_evals_per_step": statistics.mean(ens["mixed"]["evals"]),
+        "fp64": {"value": v["fp64"], "ms_per_step": ens["fp64"]["ms"] / steps,
+                 "max_abs_rel_dE": ens["fp64"]["drift"],
+                 "mean_map_evals_per_step": statistics.mean(ens["fp64"]["evals"])},
+    }
+    if "single_fp64" in ens:
+        summ["plain_fp64_single_contexts"] = {
+            "value": v["single_fp64"], "ms_per_step": ens["single_fp64"]["ms"] / steps,
+            "max_abs_rel_dE": ens["single_fp64"]["drift"]}
+        summ["speedup_mixed_batch_vs_plain_fp64"] = v["mixed"] / v["single_fp64"]
+        summ["speedup_fp64_batch_vs_plain_fp64"] = v["fp64"] / v["single_fp64"]
+    return summ
 
 
 # ---------------------------------------------------------------- oracle (CPU) arm
@@ -444,8 +623,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--only", choices=["fp64", "mixed"], default=None,
-                    help="profiling run of one precision path (prints no report line)")
+    ap.add_argument("--only", choices=["fp64", "mixed", "ensemble", "large"], default=None,
+                    help="profiling run of one path (prints no report line)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 67M-particle case")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling run without the e2e arm")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -90,6 +90,16 @@ typedef struct {
                                    orbit velocity (fewer inner iterations; H(j) then
                                    depends on the history at the inner tolerance, so
                                    use it with inner_tol_scale < 1) */
+  int order;                    /* B-spline degree r of the particle shape: 2 (default,
+                                   the paper's production runs, C^1) or 1 (the linear
+                                   shapes of the Sec. 5.3 comparison, knots on the nodes) */
+  int refine_max;               /* convergence-triggered particle refinement (Sec. 5.3):
+                                   a particle whose inner solve fails is retried with
+                                   2, 4, .. 2^refine_max equal substeps of the (fixed)
+                                   field step, each substep seeing the time-linear
+                                   potential of Eq. A-g-s and depositing its orbit
+                                   current weighted by its share of the step; 0..3,
+                                   default 0 (off) */
 } pic_options;
 
 /* Per-step report (Sec. 4.4 diagnostics and solver counters). */
@@ -103,6 +113,8 @@ typedef struct {
   int outer_iters, map_evals, inner_max;
   double inner_mean;            /* inner iterations of the final map evaluation */
   int status;                   /* return code of the step */
+  int refined;                  /* particles of the final map evaluation that needed
+                                   substeps (refine_max > 0) */
 } pic_report;
 
 /* Fill *opt with the paper's defaults (see pic_options). */
@@ -156,6 +168,11 @@ int64_t pic_num_particles(const pic_ctx *ctx);
 int pic_get_particles(pic_ctx *ctx, double *x, double *P, double *w,
                       int32_t *species, int on_device);
 
+/* Proper velocities u = p / m (so v = u / gamma) of the accepted particles,
+   with the mechanical momentum p = P - q A_h(x) (Eq. rel-P-def), in load
+   order: 3*N values, component-major. */
+int pic_get_velocities(pic_ctx *ctx, double *u, int on_device);
+
 /* Copy the accepted mesh state out: phi, psi, rho (Ng), A, U (3*Ng) at the
    current time level and J (3*Ng), the accepted current J^{n-1/2} that seeds
    the next outer iteration.  Any pointer may be NULL. */
@@ -182,6 +199,7 @@ typedef struct {
   int64_t pushes;        /* particles x map evaluations */
   int64_t inner_iters;   /* summed inner Picard iterations */
   int64_t pieces;        /* summed knot-split orbit pieces walked (gathers and deposits) */
+  int64_t refined;       /* particle solves that needed substeps (refine_max > 0) */
 } pic_stats;
 
 int pic_get_stats(const pic_ctx *ctx, pic_stats *out);
@@ -206,6 +224,7 @@ int pic_fma_throughput(int precision, double *flops_per_s);
    with DEVICE arrays sp (n int32, NULL = species 0), x (dim*n absolute
    positions), P (3*n canonical momenta), w (n weights), A (3*Ng vector
    potential, layout as in pic_get_potentials); *K_out is a HOST double.
+   The interpolation A_h uses the quadratic shape (order 2, the default).
    All work is queued on cuda_stream (NULL = legacy default stream) and the
    call returns after that stream has finished it.
    Scratch: a fixed 128 KiB array of device memory inside the library, which
@@ -225,6 +244,74 @@ int pic_kinetic_energy_noalloc(const pic_grid *grid, const pic_species *species,
 
 const char *pic_last_error(const pic_ctx *ctx);
 void pic_free(pic_ctx *ctx);
+
+/* ---- batched ensembles of 1D3V problems -----------------------------------
+ *
+ * A pic_batch advances B independent one-dimensional (1D3V) problems with
+ * one implicit step each per call: the step of pic_step (Algorithm 1 with the
+ * GM-HC push, orbit deposit and CN field solve of Sec. 2-4) applied to every
+ * instance, with every phase of the step run as one GPU launch over all
+ * instances and the outer solver's decisions (accept, backtrack, Anderson or
+ * damped Picard, verify) taken on the device per instance.  The paper has no
+ * ensemble driver; each instance computes exactly what a single-problem
+ * context with the same grid, particles, species, dt and options computes
+ * (up to the summation order of its reductions).
+ *
+ * Instances share the species, dt and options and differ in their mesh
+ * (n[b] nodes, a power of two 4..1024, on [x0[b], x0[b] + L[b])) and
+ * particles (np[b], 0 allowed).  Every array below is in HOST memory, and
+ * the layouts are those of the single-problem calls with dim = 1.  The batch
+ * owns all device memory; options.cuda_stream selects the stream (NULL = a
+ * stream the batch creates).  options.anderson_m may be at most 8.
+ * Not thread-safe. */
+typedef struct pic_batch pic_batch;
+
+/* Create a batch of B instances (1 <= B <= 65536).  x0 may be NULL (all 0);
+   opt may be NULL for the defaults.  Returns PIC_EARG for invalid sizes or
+   options, PIC_ENOMEM if the device allocations fail. */
+int pic_batch_init(pic_batch **out, int B, const int *n, const double *L, const double *x0,
+                   const int64_t *np, const pic_species *species, int nspecies, double dt,
+                   const pic_options *opt);
+
+/* Stage the initial data of instance inst (0 <= inst < B): np[inst]
+   particles as for pic_set_particles with is_canonical = 0 (species may be
+   NULL; x: np absolute positions; u: 3*np proper velocities; w: np weights)
+   and the potentials A, U (3*n[inst] each, NULL = zero) as for
+   pic_set_potentials.  The data are copied; pic_batch_start consumes them. */
+int pic_batch_set_instance(pic_batch *b, int inst, const int32_t *species, const double *x,
+                           const double *u, const double *w, const double *A, const double *U);
+
+/* pic_start for every instance (projection, P from u, rho^0 and J^0, the
+   initial constraints, the reference energy).  Every instance must have been
+   staged (else PIC_ESTATE).  reports: B entries or NULL. */
+int pic_batch_start(pic_batch *b, pic_report *reports);
+
+/* One implicit step of every instance with tau_rel = tol, tau_abs =
+   tol*tol_abs_ratio.  Instances whose step fails keep their accepted state
+   (as pic_step does) and report PIC_EINNER / PIC_EOUTER in their
+   pic_report.status; the others commit.  Returns PIC_OK when every instance
+   succeeded, else the status of the first failed instance.
+   reports: B entries or NULL. */
+int pic_batch_step(pic_batch *b, double tol, pic_report *reports);
+
+int64_t pic_batch_num_particles(const pic_batch *b, int inst);
+
+/* The accepted particles of one instance in load order (x: np; P: 3*np
+   canonical momenta; w: np; species: np int32).  Any pointer may be NULL. */
+int pic_batch_get_particles(pic_batch *b, int inst, double *x, double *P, double *w,
+                            int32_t *species);
+
+/* The accepted mesh state of one instance as in pic_get_potentials
+   (phi, psi, rho: n; A, U, J: 3*n).  Any pointer may be NULL. */
+int pic_batch_get_potentials(pic_batch *b, int inst, double *phi, double *psi, double *A,
+                             double *U, double *rho, double *J);
+
+/* Work counters as pic_get_stats (map_ms is not measured: 0). */
+int pic_batch_get_stats(const pic_batch *b, pic_stats *out);
+int pic_batch_reset_stats(pic_batch *b);
+
+const char *pic_batch_last_error(const pic_batch *b);
+void pic_batch_free(pic_batch *b);
 
 #ifdef __cplusplus
 }

@@ -26,8 +26,11 @@ PIC_FP64, PIC_MIXED = 0, 1
 # every symbol include/pic.h declares (checked by the CPU test suite)
 EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
            "pic_start", "pic_step", "pic_eval_map", "pic_num_particles", "pic_get_particles",
-           "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
-           "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free")
+           "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
+           "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free",
+           "pic_batch_init", "pic_batch_set_instance", "pic_batch_start", "pic_batch_step",
+           "pic_batch_num_particles", "pic_batch_get_particles", "pic_batch_get_potentials",
+           "pic_batch_get_stats", "pic_batch_reset_stats", "pic_batch_last_error", "pic_batch_free")
 
 
 class Grid(C.Structure):
@@ -47,12 +50,14 @@ class Options(C.Structure):
         ("decrease_coef", C.c_double), ("growth_limit", C.c_double), ("tol_abs_ratio", C.c_double),
         ("inner_tol_scale", C.c_double), ("precision", C.c_int), ("mixed_tol_floor", C.c_double),
         ("sort_every", C.c_int), ("cuda_stream", C.c_void_p), ("inner_warm_start", C.c_int),
+        ("order", C.c_int), ("refine_max", C.c_int),
     ]
 
 
 class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("map_launches", C.c_int64), ("map_ms", C.c_double),
-                ("pushes", C.c_int64), ("inner_iters", C.c_int64), ("pieces", C.c_int64)]
+                ("pushes", C.c_int64), ("inner_iters", C.c_int64), ("pieces", C.c_int64),
+                ("refined", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -64,7 +69,7 @@ class Report(C.Structure):
         ("gauss_rms", C.c_double), ("lorenz_rms", C.c_double), ("work_residual", C.c_double),
         ("chain_rms", C.c_double), ("res_scaled_rms", C.c_double), ("res_scaled_max", C.c_double),
         ("outer_iters", C.c_int), ("map_evals", C.c_int), ("inner_max", C.c_int),
-        ("inner_mean", C.c_double), ("status", C.c_int),
+        ("inner_mean", C.c_double), ("status", C.c_int), ("refined", C.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -94,6 +99,7 @@ def lib():
         L.pic_num_particles.argtypes = [_VP]
         L.pic_get_particles.argtypes = [_VP, _VP, _VP, _VP, _VP, C.c_int]
         L.pic_get_potentials.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int]
+        L.pic_get_velocities.argtypes = [_VP, _VP, C.c_int]
         L.pic_set_state.argtypes = [_VP, C.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                     _VP, C.c_double, C.c_int]
         L.pic_get_stats.argtypes = [_VP, C.POINTER(Stats)]
@@ -105,6 +111,20 @@ def lib():
         L.pic_last_error.restype = C.c_char_p
         L.pic_last_error.argtypes = [_VP]
         L.pic_free.argtypes = [_VP]
+        L.pic_batch_init.argtypes = [C.POINTER(_VP), C.c_int, _VP, _VP, _VP, _VP,
+                                     C.POINTER(Species), C.c_int, C.c_double, C.POINTER(Options)]
+        L.pic_batch_set_instance.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]
+        L.pic_batch_start.argtypes = [_VP, _VP]
+        L.pic_batch_step.argtypes = [_VP, C.c_double, _VP]
+        L.pic_batch_num_particles.restype = C.c_int64
+        L.pic_batch_num_particles.argtypes = [_VP, C.c_int]
+        L.pic_batch_get_particles.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP]
+        L.pic_batch_get_potentials.argtypes = [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]
+        L.pic_batch_get_stats.argtypes = [_VP, C.POINTER(Stats)]
+        L.pic_batch_reset_stats.argtypes = [_VP]
+        L.pic_batch_last_error.restype = C.c_char_p
+        L.pic_batch_last_error.argtypes = [_VP]
+        L.pic_batch_free.argtypes = [_VP]
         _lib = L
     return _lib
 
@@ -235,6 +255,12 @@ class Simulation:
                                             _ptr(sp, 0), 0))
         return x.reshape(self.dim, npart), P.reshape(3, npart), w, sp
 
+    def velocities(self):
+        """Proper velocities u = p / m of the particles, shape (3, N), load order."""
+        u = np.zeros(3 * self.num_particles())
+        self._check(lib().pic_get_velocities(self._h, _ptr(u, 0), 0))
+        return u.reshape(3, -1)
+
     def fields(self) -> dict:
         N = self.Ng
         out = dict(phi=np.zeros(N), psi=np.zeros(N), A=np.zeros(3 * N), U=np.zeros(3 * N),
@@ -268,6 +294,118 @@ class Simulation:
     @property
     def handle(self):
         return self._h
+
+
+def _reports_to_dicts(arr, n):
+    return [arr[b].as_dict() for b in range(n)]
+
+
+class Batch:
+    """An ensemble of independent 1D3V problems advanced together (pic_batch_*).
+
+    ``n``, ``L``, ``x0`` and ``np_`` give every instance's mesh size, length,
+    origin and particle count; the species, dt and options are shared."""
+
+    def __init__(self, n, L, x0, np_, species, dt, precision=PIC_FP64, stream=None, **opts):
+        self.B = len(n)
+        self.n = np.ascontiguousarray(n, np.int32)
+        self.L = np.ascontiguousarray(L, np.float64)
+        self.x0 = np.ascontiguousarray(x0, np.float64)
+        self.np_ = np.ascontiguousarray(np_, np.int64)
+        sp = (Species * len(species))(*[Species(float(q), float(m)) for q, m in species])
+        o = default_options()
+        o.precision = precision
+        for k, v in opts.items():
+            setattr(o, "lambda_" if k == "lambda" else k, v)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = None
+        o.cuda_stream = stream or None
+        h = C.c_void_p()
+        rc = lib().pic_batch_init(C.byref(h), self.B, _ptr(self.n, 0), _ptr(self.L, 0),
+                                  _ptr(self.x0, 0), _ptr(self.np_, 0), sp, len(species),
+                                  float(dt), C.byref(o))
+        if rc:
+            raise PicError(rc, "pic_batch_init rejected the arguments or could not allocate")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc and rc not in allow:
+            raise PicError(rc, lib().pic_batch_last_error(self._h).decode())
+        return rc
+
+    def set_instance(self, b, x, u, w, species=None, A=None, U=None):
+        x = np.ascontiguousarray(x, np.float64).reshape(-1)
+        u = np.ascontiguousarray(u, np.float64)
+        w = np.ascontiguousarray(w, np.float64)
+        species = None if species is None else np.ascontiguousarray(species, np.int32)
+        A = None if A is None else np.ascontiguousarray(A, np.float64)
+        U = None if U is None else np.ascontiguousarray(U, np.float64)
+        self._check(lib().pic_batch_set_instance(self._h, int(b), _ptr(species, 0), _ptr(x, 0),
+                                                 _ptr(u, 0), _ptr(w, 0), _ptr(A, 0), _ptr(U, 0)))
+
+    def start(self) -> list:
+        reps = (Report * self.B)()
+        self._check(lib().pic_batch_start(self._h, reps))
+        return _reports_to_dicts(reps, self.B)
+
+    def step(self, tol) -> list:
+        """One step of every instance; per-instance reports (status included)."""
+        reps = (Report * self.B)()
+        rc = lib().pic_batch_step(self._h, float(tol), reps)
+        self._check(rc, allow=(PIC_EINNER, PIC_EOUTER))
+        return _reports_to_dicts(reps, self.B)
+
+    def particles(self, b):
+        npart = int(self.np_[b])
+        x = np.zeros(npart); P = np.zeros(3 * npart); w = np.zeros(npart)
+        sp = np.zeros(npart, np.int32)
+        self._check(lib().pic_batch_get_particles(self._h, int(b), _ptr(x, 0), _ptr(P, 0),
+                                                  _ptr(w, 0), _ptr(sp, 0)))
+        return x.reshape(1, npart), P.reshape(3, npart), w, sp
+
+    def fields(self, b) -> dict:
+        N = int(self.n[b])
+        out = dict(phi=np.zeros(N), psi=np.zeros(N), A=np.zeros(3 * N), U=np.zeros(3 * N),
+                   rho=np.zeros(N), J=np.zeros(3 * N))
+        self._check(lib().pic_batch_get_potentials(self._h, int(b), *[_ptr(out[k], 0) for k in
+                                                   ("phi", "psi", "A", "U", "rho", "J")]))
+        return out
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(lib().pic_batch_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def reset_stats(self):
+        self._check(lib().pic_batch_reset_stats(self._h))
+
+
+def batch_from_configs(cfgs, precision=PIC_FP64, **opts) -> Batch:
+    """Create and load a batch from a list of 1D ``pic_inputs`` recipes that
+    share species, dt and rho_bg."""
+    c0 = cfgs[0]
+    bt = Batch([c["n"][0] for c in cfgs], [c["L"][0] for c in cfgs], [c["x0"][0] for c in cfgs],
+               [c["w"].shape[0] for c in cfgs], c0["species"], c0["dt"], precision=precision,
+               rho_bg=c0["rho_bg"], **opts)
+    for b, c in enumerate(cfgs):
+        bt.set_instance(b, c["x"], c["u"], c["w"], c["sp"], c["A"], c["U"])
+    return bt
 
 
 def fma_throughput(precision=PIC_FP64) -> float:

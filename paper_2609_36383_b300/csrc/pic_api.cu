@@ -16,8 +16,6 @@
 #include <new>
 #include <vector>
 
-namespace {
-
 // Gauss-Legendre nodes/weights on [0, 1] (Newton on the Legendre recurrence).
 void gauss_legendre01(int n, double *t, double *w) {
   for (int i = 0; i < n; i++) {
@@ -49,6 +47,8 @@ void gauss_legendre01(int n, double *t, double *w) {
     t[i] = 0.5 * (1.0 - z);
   }
 }
+
+namespace {
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 int ilog2(int n) { int l = 0; while ((1 << l) < n) l++; return l; }
@@ -136,6 +136,8 @@ StepConst make_sc(const pic_ctx *ctx, double itr, double ita) {
   sc.inner_max = ctx->opt.inner_max;
   sc.ngl = ctx->opt.gl_points > 0 ? ctx->opt.gl_points : ctx->g.dim + 1;
   sc.warm = ctx->opt.inner_warm_start ? 1 : 0;
+  sc.order = ctx->opt.order;
+  sc.refine_max = ctx->opt.refine_max;
   gauss_legendre01(sc.ngl, sc.gl_t, sc.gl_w);
   return sc;
 }
@@ -352,6 +354,8 @@ void pic_default_options(pic_options *o) {
   o->sort_every = 10;
   o->cuda_stream = nullptr;
   o->inner_warm_start = 0;
+  o->order = 2;
+  o->refine_max = 0;
 }
 
 int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, int nspecies,
@@ -372,7 +376,8 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, in
   if (o.gl_points < 0 || o.gl_points > PIC_MAX_GL || o.inner_max < 1 || o.outer_max < 1 ||
       o.anderson_m < 0 || o.anderson_m > PIC_MAX_ANDERSON || o.backtrack_levels < 1 ||
       (o.precision != PIC_FP64 && o.precision != PIC_MIXED) || !(o.kappa > 0.0) ||
-      !(o.sigma1 > 0.0) || !(o.sigma2 > 0.0))
+      !(o.sigma1 > 0.0) || !(o.sigma2 > 0.0) || (o.order != 1 && o.order != 2) ||
+      o.refine_max < 0 || o.refine_max > 3)
     return PIC_EARG;
   pic_ctx *ctx = new (std::nothrow) pic_ctx();
   if (!ctx) return PIC_ENOMEM;
@@ -440,12 +445,14 @@ int pic_get_stats(const pic_ctx *ctx, pic_stats *out) {
   out->pushes = ctx->pushes;
   out->inner_iters = ctx->inner_iters;
   out->pieces = ctx->pieces;
+  out->refined = ctx->refined;
   return PIC_OK;
 }
 
 int pic_reset_stats(pic_ctx *ctx) {
   if (!ctx) return PIC_EARG;
   ctx->launches = ctx->map_launches = ctx->pushes = ctx->inner_iters = ctx->pieces = 0;
+  ctx->refined = 0;
   ctx->map_ms = 0.0;
   return PIC_OK;
 }
@@ -693,6 +700,7 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
     R.chain_rms = ctx->np ? std::sqrt(ev.chain / (3.0 * ctx->np)) : 0.0;
     R.inner_max = ev.cnt.inner_max;
     R.inner_mean = ctx->np ? (double)ev.cnt.inner_sum / ctx->np : 0.0;
+    R.refined = (int)ev.cnt.refined;
     if ((e = particles_commit(ctx))) return e;
     std::swap(ctx->phi_h, ctx->phi1_h);
     std::swap(ctx->psi_h, ctx->psi1_h);
@@ -717,6 +725,11 @@ int pic_get_particles(pic_ctx *ctx, double *x, double *P, double *w, int32_t *sp
                       int on_device) {
   if (!ctx) return PIC_EARG;
   return particles_export(ctx, x, P, w, species, on_device);
+}
+
+int pic_get_velocities(pic_ctx *ctx, double *u, int on_device) {
+  if (!ctx || !u) return PIC_EARG;
+  return particles_export_u(ctx, u, on_device);
 }
 
 int pic_get_potentials(pic_ctx *ctx, double *phi, double *psi, double *A, double *U, double *rho,

@@ -39,6 +39,8 @@ struct StepConst {
   int inner_max;
   int ngl;
   int warm;  // start the inner iteration from vbar instead of v^0
+  int order;       // shape degree: 2, or 1
+  int refine_max;  // convergence-triggered refinement depth (0 = off)
   double gl_t[PIC_MAX_GL], gl_w[PIC_MAX_GL];  // nodes and weights on [0, 1]
 };
 
@@ -48,6 +50,7 @@ struct EvalCounters {
   int inner_max;
   unsigned long long inner_sum;
   unsigned long long pieces;
+  unsigned long long refined;  // particles solved with substeps
 };
 
 // Reduction partials returned to the host after the residual kernel.
@@ -124,6 +127,7 @@ struct pic_ctx {
   long long pushes;            // particles x map evaluations
   long long inner_iters;       // summed inner iterations
   long long pieces;            // summed knot-split orbit pieces walked
+  long long refined;           // particle solves that needed substeps
   cudaEvent_t ev0, ev1;
   int num_sms;
   // ---- execution -----------------------------------------------------------
@@ -140,6 +144,9 @@ struct pic_ctx {
   int ngraphs;
   int graphs_off;  // capture failed once: launch directly
 };
+
+// Gauss-Legendre nodes t and weights w of an n-point rule on [0, 1]
+void gauss_legendre01(int n, double *t, double *w);
 
 // drop every captured graph (buffers or sizes changed)
 void graphs_clear(pic_ctx *ctx);
@@ -202,6 +209,7 @@ int particles_export(pic_ctx *ctx, double *x, double *P, double *w, int32_t *sp,
                      int on_device);
 int particles_export_eval(pic_ctx *ctx, double *vbar, double *Pnew, int32_t *iters,
                           int on_device);
+int particles_export_u(pic_ctx *ctx, double *u, int on_device);
 int particles_sort(pic_ctx *ctx);
 
 // ---------------------------------------------------------------- reduce.cu

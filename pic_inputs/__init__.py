@@ -24,6 +24,8 @@ workload sizes used here):
   each cell, random-phase A_z seed noise of amplitude 1e-4 over 1 <= |k| <= 8.
 - ``weibel_2d_ions``: the large case with a mobile ion species of mass ratio
   100 at rest (same temperature in energy units) and no background.
+- ``two_stream_ensemble``: many independent ``two_stream_1d`` instances with
+  drawn mesh sizes, particles per cell and beam velocities.
 """
 from __future__ import annotations
 
@@ -302,6 +304,25 @@ def weibel_3d(n=32, pairs=25, v0=0.9, B0=1e-4, dt=0.04, tol=1e-11, steps=2500, *
                 species=[(-1.0, 1.0)], rho_bg=1.0, dt=dt, tol=tol, steps=steps,
                 x=np.concatenate(xs, axis=1), u=np.concatenate(us, axis=1), w=w,
                 sp=np.zeros(N, np.int32), A=A, U=U)
+
+
+def two_stream_ensemble(B=256, seed=0, nx_choices=(32, 64, 128, 256, 512), ppc_range=(16, 256),
+                        u_range=(0.2, 0.95), dt=0.1, tol=1e-10, steps=1000, pert=1e-3):
+    """An ensemble of B independent 1D3V two-stream instances on L = 4 pi
+    (k = 0.5): per instance a mesh size drawn uniformly from ``nx_choices``, an
+    even particle count per cell drawn uniformly from ``ppc_range`` (half per
+    beam), a beam proper velocity u drawn uniformly from ``u_range``, and its
+    own storage-order seed.  Each instance is ``two_stream_1d`` with those
+    values."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(B):
+        nx = int(rng.choice(nx_choices))
+        ppc = int(rng.integers(ppc_range[0] // 2, ppc_range[1] // 2 + 1)) * 2
+        u0 = float(rng.uniform(*u_range))
+        out.append(two_stream_1d(nx=nx, ppc_beam=ppc // 2, u0=u0, k=0.5, pert=pert, dt=dt,
+                                 tol=tol, steps=steps, seed=seed * 100003 + b))
+    return out
 
 
 def random_fields(rng, Ng, scale=1e-2):

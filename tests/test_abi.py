@@ -47,6 +47,7 @@ def test_default_options_are_the_papers(libpic):
     assert (o.beta, o.lambda_, o.decrease_coef, o.growth_limit) == (0.5, 1e-12, 1e-4, 1.2)
     assert o.backtrack_levels == 7 and o.project_nyquist == 1
     assert (o.kappa, o.sigma1, o.sigma2) == (1.0, 1.0, 1.0)
+    assert o.order == 2 and o.refine_max == 0  # quadratic shapes, no refinement
 
 
 def test_init_rejects_bad_grids_without_touching_the_gpu(libpic):
@@ -61,3 +62,17 @@ def test_init_rejects_bad_grids_without_touching_the_gpu(libpic):
     g.n[0] = 64
     assert P.lib().pic_init(ctypes.byref(h), ctypes.byref(g), sp, 1, -0.1, None) == P.PIC_EARG
     assert P.lib().pic_init(ctypes.byref(h), ctypes.byref(g), sp, 0, 0.1, None) == P.PIC_EARG
+
+
+def test_batch_init_rejects_bad_sizes_without_touching_the_gpu(libpic):
+    import paper_2609_36383_b300 as P
+    h = ctypes.c_void_p()
+    sp = (P.Species * 1)(P.Species(-1.0, 1.0))
+    n = (ctypes.c_int * 2)(16, 24)  # 24 is not a power of two
+    L = (ctypes.c_double * 2)(1.0, 1.0)
+    npart = (ctypes.c_int64 * 2)(10, 10)
+    assert P.lib().pic_batch_init(ctypes.byref(h), 2, n, L, None, npart, sp, 1, 0.1,
+                                  None) == P.PIC_EARG
+    n[1] = 2048  # above the largest instance mesh
+    assert P.lib().pic_batch_init(ctypes.byref(h), 2, n, L, None, npart, sp, 1, 0.1,
+                                  None) == P.PIC_EARG

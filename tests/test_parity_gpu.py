@@ -107,6 +107,17 @@ def test_start_parity(case):
     assert rs["gauss_rms"] < 1e-12 and rs["lorenz_rms"] < 1e-12
 
 
+def test_velocities_round_trip(case):
+    """pic_get_velocities returns u = (P - q A_h(x)) / m: right after start it
+    recovers the loaded proper velocities (P was formed as m u + q A_h(x))."""
+    name, cfg = case
+    s = make_gpu(cfg)
+    s.start()
+    u = s.velocities()
+    scale = max(np.abs(cfg["u"]).max(), 1e-30)
+    assert np.abs(u - cfg["u"]).max() <= 1e-13 * scale
+
+
 def test_single_map_evaluation_parity(case):
     """H(j), vbar, P^{n+1} and inner counts of one evaluation (Sec. 4.5)."""
     name, cfg = case
