@@ -26,10 +26,12 @@
 //   k_bresid   one CTA per instance: H = P J_orb, r = H - j, the sums of Eq.
 //              mixed-nonlinear-tests, the Gram products the next Anderson
 //              solve needs, and (final pass) the particle and mesh work.
-// The round is captured once into a CUDA graph; the host replays it a few
-// times, then reads how many instances are still running (one copy).  A step
-// ends when no instance runs; instances that finished early skip the rest of
-// the rounds.  Every instance then commits (or, on failure, keeps) its state
+// A step is one CUDA graph launch for all its rounds: a conditional while
+// node repeats the round, and k_bctl clears the node's condition once no
+// instance evaluates (or at a round limit that Algorithm 1 cannot reach), so
+// the host waits once per step.  Instances that finished early skip the rest
+// of the rounds.  Where the driver cannot build that graph, the host launches
+// the rounds itself and reads the loop state after each.  Every instance then commits (or, on failure, keeps) its state
 // exactly as a single-problem context does (pic_step).
 //
 // Per-instance initial states (pic_start) are prepared by a temporary
@@ -91,6 +93,14 @@ struct BRes {
   double work_mesh, work_p, chain;
 };
 
+// progress of the round loop of one step (device-resident)
+struct BLoop {
+  int running;   // instances that evaluate in the current round
+  int rounds;    // rounds started in this step
+  int overflow;  // the round limit was reached with instances still running
+  int pad;
+};
+
 struct BParams {  // solver constants of the batch
   int M, anderson_start, levels, outer_max;
   double beta, lambda, dc, growth;
@@ -116,7 +126,6 @@ struct pic_batch {
   int nblocks;
   int started;
   long long steps_done;
-  int last_rounds;
   // staged host inputs (pic_batch_set_instance), consumed by pic_batch_start
   struct Stage {
     std::vector<int32_t> sp;
@@ -132,7 +141,7 @@ struct pic_batch {
   BState *d_state, *h_state;  // h_state pinned
   BRes *d_res;
   EvalCounters *d_cnt;
-  int32_t *d_running, *h_running;  // pinned
+  BLoop *d_loop, *h_loop;  // h_loop pinned
   // particles
   int32_t *cell, *sp, *iters, *keys, *cnt_sort;
   int64_t *id, *slot;
@@ -148,10 +157,11 @@ struct pic_batch {
   double2 *tw;
   double *d_diag, *h_diag;  // per instance: K, W, gauss, lorenz (pinned host copy)
   double *d_out;            // export scratch
-  // execution
-  cudaGraphExec_t round_exec;
+  // execution: the rounds of a step run as one graph whose while node
+  // repeats the round until the controller reports no instance running
+  cudaGraphExec_t loop_exec;
   double graph_tr, graph_ta, graph_itr, graph_ita;
-  int graph_ok;  // 1 captured, 0 not yet, -1 capture failed: launch directly
+  int graph_ok;  // 1 built, 0 not yet, -1 unavailable: host-driven rounds
   long long launches, map_launches, pushes, inner_iters, pieces, refined;
 };
 
@@ -338,18 +348,17 @@ __device__ void outer_top(BState &s, const BParams &bp) {
 __global__ void __launch_bounds__(kCtlThreads)
 k_bctl(int B, BState *__restrict__ states, const BRes *__restrict__ res,
        const EvalCounters *__restrict__ cnts, const BInst *__restrict__ inst, BParams bp,
-       int32_t *__restrict__ running) {
+       BLoop *__restrict__ loop, int max_rounds, cudaGraphConditionalHandle cond) {
   __shared__ int s_run;
   if (threadIdx.x == 0) s_run = 0;
   __syncthreads();
   int run = 0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
-    BState s = states[b];
+    BState &s = states[b];  // worked on in place: the state is too large for registers
     s.accept = 0;
     s.seed = 0;
     if (s.phase != B_RUNNING) {
       s.mode = B_IDLE;
-      states[b] = s;
       continue;
     }
     const BRes R = res[b];
@@ -454,16 +463,29 @@ k_bctl(int B, BState *__restrict__ states, const BRes *__restrict__ res,
         break;
     }
     if (s.phase == B_RUNNING && s.mode != B_IDLE) run++;
-    states[b] = s;
   }
   atomicAdd(&s_run, run);
   __syncthreads();
-  if (threadIdx.x == 0) *running = s_run;
+  if (threadIdx.x == 0) {
+    // the loop ends when no instance evaluates, or (never expected: Algorithm
+    // 1 takes at most 2 + outer_max (2 levels + 1) evaluations) at the limit
+    const int r = loop->rounds + 1;
+    loop->rounds = r;
+    loop->running = s_run;
+    const bool more = s_run > 0 && r < max_rounds;
+    if (s_run > 0 && !more) loop->overflow = 1;
+    if (cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
 }
 
 // start of a step: every instance runs Algorithm 1 from its first evaluation
-__global__ void k_bbegin(int B, BState *states) {
+__global__ void k_bbegin(int B, BState *states, BLoop *loop) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) {
+    loop->running = B;
+    loop->rounds = 0;
+    loop->overflow = 0;
+  }
   if (b >= B) return;
   BState s;
   memset(&s, 0, sizeof s);
@@ -1141,12 +1163,20 @@ size_t field_smem(const pic_batch *bt) {
 }
 
 // the kernels of one round (see the file comment)
+// rounds a step may take: every round is one evaluation per running
+// instance, Algorithm 1 needs at most 2 + outer_max (2 levels + 1) of them,
+// and one more round finds no instance running
+int max_rounds(const pic_batch *bt) {
+  return 4 + bt->opt.outer_max * (2 * bt->opt.backtrack_levels + 1);
+}
+
 template <typename T>
-int enqueue_round(pic_batch *bt, double tr, double ta, double itr, double ita) {
+int enqueue_round(pic_batch *bt, double tr, double ta, double itr, double ita,
+                  cudaGraphConditionalHandle cond) {
   const int B = bt->B;
   const BMesh m = b_mesh(bt);
   k_bctl<<<1, kCtlThreads, 0, bt->st>>>(B, bt->d_state, bt->d_res, bt->d_cnt, bt->d_inst,
-                                         b_params(bt, tr, ta), bt->d_running);
+                                         b_params(bt, tr, ta), bt->d_loop, max_rounds(bt), cond);
   BKCHECK();
   k_baccept<<<B, kBT, 0, bt->st>>>(m);
   BKCHECK();
@@ -1199,63 +1229,85 @@ int enqueue_round(pic_batch *bt, double tr, double ta, double itr, double ita) {
   }
   k_bresid<<<B, kBT, 0, bt->st>>>(m, tr, ta, bt->opt.project_nyquist);
   BKCHECK();
-  BCK(cudaMemcpyAsync(bt->h_running, bt->d_running, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                      bt->st));
   return PIC_OK;
 }
 
-// queue one round: replay the captured graph (capturing it on first use)
-int b_round(pic_batch *bt, double tr, double ta, double itr, double ita) {
+// Build the graph of a step's round loop: one conditional while node whose
+// body is the round, captured from the same launches the host-driven
+// fallback makes; k_bctl sets the node's condition.  Returns false (and
+// leaves no error pending) if the driver cannot build it.
+bool build_loop_graph(pic_batch *bt, double tr, double ta, double itr, double ita) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  cudaGraphConditionalHandle cond = 0;
+  if (ok) ok = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) ==
+               cudaSuccess;
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node = nullptr;
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  if (ok) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(bt->st, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const long long before = bt->launches, mbefore = bt->map_launches;
+      const int e = bt->rsize == 8 ? enqueue_round<double>(bt, tr, ta, itr, ita, cond)
+                                   : enqueue_round<float>(bt, tr, ta, itr, ita, cond);
+      bt->launches = before;
+      bt->map_launches = mbefore;
+      cudaGraph_t cap = nullptr;
+      ok = cudaStreamEndCapture(bt->st, &cap) == cudaSuccess && e == PIC_OK;
+    }
+  }
+  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();  // a refused build falls back to host-driven rounds
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return false;
+  }
+  if (bt->loop_exec) cudaGraphExecDestroy(bt->loop_exec);
+  bt->loop_exec = exec;
+  bt->graph_tr = tr;
+  bt->graph_ta = ta;
+  bt->graph_itr = itr;
+  bt->graph_ita = ita;
+  return true;
+}
+
+// Queue all rounds of a step.  With the loop graph, one graph launch runs
+// them with no host round trip; otherwise the host launches a round, reads
+// the loop state and repeats.
+int b_rounds(pic_batch *bt, double tr, double ta, double itr, double ita) {
   if (bt->graph_ok == 1 && (bt->graph_tr != tr || bt->graph_ta != ta || bt->graph_itr != itr ||
-                            bt->graph_ita != ita)) {
-    cudaGraphExecDestroy(bt->round_exec);
-    bt->round_exec = nullptr;
+                            bt->graph_ita != ita))
     bt->graph_ok = 0;
+  if (bt->graph_ok == 0) bt->graph_ok = build_loop_graph(bt, tr, ta, itr, ita) ? 1 : -1;
+  if (bt->graph_ok == 1) {
+    BCK(cudaGraphLaunch(bt->loop_exec, bt->st));
+    return PIC_OK;  // launches are counted from the rounds the loop reports
   }
-  auto direct = [&]() {
-    return bt->rsize == 8 ? enqueue_round<double>(bt, tr, ta, itr, ita)
-                          : enqueue_round<float>(bt, tr, ta, itr, ita);
-  };
-  if (bt->graph_ok == -1) return direct();
-  const int nkern = bt->nblocks > 0 ? 7 : 5;
-  if (bt->graph_ok == 0) {
-    const long long before = bt->launches, mbefore = bt->map_launches;
-    if (cudaStreamBeginCapture(bt->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      cudaGetLastError();
-      bt->graph_ok = -1;
-      return direct();
-    }
-    const int e = direct();
-    cudaGraph_t graph = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(bt->st, &graph);
-    bt->launches = before;
-    bt->map_launches = mbefore;
-    cudaGraphExec_t exec = nullptr;
-    if (!e && ce == cudaSuccess && graph) ce = cudaGraphInstantiate(&exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
-    if (e || ce != cudaSuccess || !exec) {
-      cudaGetLastError();
-      bt->graph_ok = -1;
-      if (e && e != PIC_ECUDA) return e;
-      return direct();
-    }
-    bt->round_exec = exec;
-    bt->graph_ok = 1;
-    bt->graph_tr = tr;
-    bt->graph_ta = ta;
-    bt->graph_itr = itr;
-    bt->graph_ita = ita;
+  for (;;) {
+    const int e = bt->rsize == 8 ? enqueue_round<double>(bt, tr, ta, itr, ita, 0)
+                                 : enqueue_round<float>(bt, tr, ta, itr, ita, 0);
+    if (e) return e;
+    BCK(cudaMemcpyAsync(bt->h_loop, bt->d_loop, sizeof(BLoop), cudaMemcpyDeviceToHost, bt->st));
+    BCK(cudaStreamSynchronize(bt->st));
+    if (bt->h_loop->running == 0 || bt->h_loop->overflow) return PIC_OK;
   }
-  BCK(cudaGraphLaunch(bt->round_exec, bt->st));
-  bt->launches += nkern;
-  if (bt->nblocks > 0) bt->map_launches += 2;
-  return PIC_OK;
 }
 
 template <typename T>
 int b_step_start(pic_batch *bt) {
   const int B = bt->B;
-  k_bbegin<<<(B + 255) / 256, 256, 0, bt->st>>>(B, bt->d_state);
+  k_bbegin<<<(B + 255) / 256, 256, 0, bt->st>>>(B, bt->d_state, bt->d_loop);
   BKCHECK();
   if (bt->nblocks > 0) {
     k_bstep_start<T><<<bt->nblocks, kPT, 0, bt->st>>>(
@@ -1339,9 +1391,9 @@ int b_sort(pic_batch *bt) {
 }
 
 void b_free_all(pic_batch *bt) {
-  if (bt->round_exec) cudaGraphExecDestroy(bt->round_exec);
+  if (bt->loop_exec) cudaGraphExecDestroy(bt->loop_exec);
   void *dev[] = {bt->d_inst, bt->d_pg, bt->d_invdx, bt->d_blk2inst, bt->d_state, bt->d_res,
-                 bt->d_cnt, bt->d_running, bt->cell, bt->sp, bt->iters, bt->keys, bt->cnt_sort,
+                 bt->d_cnt, bt->d_loop, bt->cell, bt->sp, bt->iters, bt->keys, bt->cnt_sort,
                  bt->id, bt->slot, bt->off, bt->P, bt->Am, bt->v0, bt->vbar, bt->Pnew, bt->tmp_r,
                  bt->w, bt->psum, bt->phi_h, bt->psi_h, bt->rho_h, bt->A_h, bt->U_h, bt->phi1_h,
                  bt->psi1_h, bt->rho1_h, bt->A1_h, bt->U1_h, bt->A_real, bt->A1_real, bt->J_acc,
@@ -1351,7 +1403,7 @@ void b_free_all(pic_batch *bt) {
     if (p) cudaFree(p);
   if (bt->AT && bt->AT != (void *)bt->A_real) cudaFree(bt->AT);
   if (bt->h_state) cudaFreeHost(bt->h_state);
-  if (bt->h_running) cudaFreeHost(bt->h_running);
+  if (bt->h_loop) cudaFreeHost(bt->h_loop);
   if (bt->h_diag) cudaFreeHost(bt->h_diag);
   if (bt->own_st) cudaStreamDestroy(bt->own_st);
 }
@@ -1474,7 +1526,7 @@ int pic_batch_init(pic_batch **out, int B, const int *n, const double *L, const 
       {(void **)&bt->d_state, sizeof(BState) * B},
       {(void **)&bt->d_res, sizeof(BRes) * B},
       {(void **)&bt->d_cnt, sizeof(EvalCounters) * B},
-      {(void **)&bt->d_running, sizeof(int32_t)},
+      {(void **)&bt->d_loop, sizeof(BLoop)},
       {(void **)&bt->cell, sizeof(int32_t) * cap},
       {(void **)&bt->sp, sizeof(int32_t) * cap},
       {(void **)&bt->iters, sizeof(int32_t) * cap},
@@ -1537,7 +1589,7 @@ int pic_batch_init(pic_batch **out, int B, const int *n, const double *L, const 
     return PIC_ENOMEM;
   }
   if (cudaMallocHost((void **)&bt->h_state, sizeof(BState) * B) != cudaSuccess ||
-      cudaMallocHost((void **)&bt->h_running, sizeof(int32_t)) != cudaSuccess ||
+      cudaMallocHost((void **)&bt->h_loop, sizeof(BLoop)) != cudaSuccess ||
       cudaMallocHost((void **)&bt->h_diag, sizeof(double) * 4 * B) != cudaSuccess) {
     cudaGetLastError();
     b_free_all(bt);
@@ -1736,25 +1788,7 @@ int pic_batch_step(pic_batch *bt, double tol, pic_report *reports) {
   b_tolerances(bt, tol, &tr, &ta, &itr, &ita);
   int e = bt->rsize == 8 ? b_step_start<double>(bt) : b_step_start<float>(bt);
   if (e) return e;
-  // every round is one evaluation per running instance; Algorithm 1 needs at
-  // most 2 + outer_max (2 levels + 1) of them, plus the round that finds none
-  const long long max_rounds =
-      4 + (long long)bt->opt.outer_max * (2LL * bt->opt.backtrack_levels + 1);
-  long long rounds = 0;
-  int chunk = std::max(1, bt->last_rounds);
-  for (;;) {
-    for (int c = 0; c < chunk; c++)
-      if ((e = b_round(bt, tr, ta, itr, ita))) return e;
-    rounds += chunk;
-    BCK(cudaStreamSynchronize(bt->st));
-    if (*bt->h_running == 0) break;
-    if (rounds > max_rounds) {
-      bt->err = "pic_batch_step: the outer control did not finish";
-      return PIC_EOUTER;
-    }
-    chunk = 1;
-  }
-  bt->last_rounds = (int)std::min<long long>(rounds, 64);
+  if ((e = b_rounds(bt, tr, ta, itr, ita))) return e;
   if (bt->rsize == 8) {
     if ((e = b_commit_diag<double>(bt)) || (e = b_diag<double>(bt))) return e;
   } else {
@@ -1762,7 +1796,17 @@ int pic_batch_step(pic_batch *bt, double tol, pic_report *reports) {
   }
   BCK(cudaMemcpyAsync(bt->h_state, bt->d_state, sizeof(BState) * bt->B, cudaMemcpyDeviceToHost,
                       bt->st));
+  BCK(cudaMemcpyAsync(bt->h_loop, bt->d_loop, sizeof(BLoop), cudaMemcpyDeviceToHost, bt->st));
   BCK(cudaStreamSynchronize(bt->st));
+  if (bt->graph_ok == 1) {  // the host-driven rounds counted their own launches
+    const long long rounds = bt->h_loop->rounds;
+    bt->launches += rounds * (bt->nblocks > 0 ? 7 : 5);
+    if (bt->nblocks > 0) bt->map_launches += 2 * rounds;
+  }
+  if (bt->h_loop->overflow) {
+    bt->err = "pic_batch_step: the outer control did not finish within its round limit";
+    return PIC_EOUTER;
+  }
   int status = PIC_OK;
   for (int b = 0; b < bt->B; b++) {
     const BState &s = bt->h_state[b];

@@ -145,3 +145,34 @@ def test_tsi_nyquist_projection_on_off():
     assert out[0][0] > 0.1
     assert out[0][0] > 1e5 * out[1][0]
     assert out[1][2] < 1e-10 and out[0][2] < 1e-10
+
+
+@pytest.mark.skipif(os.environ.get("PIC_LONG_RUNS") != "1",
+                    reason="two 600-step 3D runs (several minutes); set PIC_LONG_RUNS=1")
+def test_tsi_shape_degree_comparison():
+    """Sec. 5.3: TSI-0.1 to T = 60 with linear (r = 1) and quadratic (r = 2)
+    shapes, projection on, the same convergence-triggered refinement policy
+    (up to 2 levels: particle steps dt/2 and dt/4).  The paper finds that
+    only the degree-one run needs refinement (first at t = 53.9); both
+    conserve energy to the solver tolerance."""
+    from oracle import closed_form as cf
+    G = cf.two_stream_rate(0.25, 0.9, math.pi / 4)
+    out = {}
+    for order in (2, 1):
+        cfg = pic_inputs.two_stream_3d(eigen_rate=G, eigen_chi=cf.chi(0.25, math.pi / 4))
+        s = make_gpu(cfg, order=order, refine_max=2)
+        s.start()
+        dE, first, total = 0.0, None, 0
+        for st in range(1, 601):
+            r = s.step(cfg["tol"])
+            assert r["status"] == 0, (order, st, r)
+            dE = max(dE, abs(r["rel_dE"]))
+            if r["refined"] and first is None:
+                first = st * cfg["dt"]
+            total += r["refined"]
+        out[order] = (first, total, dE, s.stats())
+        print(f"TSI-0.1 T=60 order={order}: first refinement at t={first}, refined particle "
+              f"solves {total}, max |dE/E| {dE:.2e}")
+        s.close()
+    assert out[2][1] == 0  # quadratic shapes never need refinement
+    assert out[2][2] < 1e-10 and out[1][2] < 1e-10
