@@ -203,9 +203,9 @@ def run_ensemble(args, rank, barrier, flush, stream):
             for n, r in zip(nps, reps):
                 if r["status"] != 0:
                     raise RuntimeError(f"ensemble step failed: {r}")
-                pushes += n * r["map_evals"]
-                drift = max(drift, abs(r["rel_dE"]))
-                evals.append(r["map_evals"])
+                pushes += n * int(r["map_evals"])
+                drift = max(drift, abs(float(r["rel_dE"])))
+                evals.append(int(r["map_evals"]))
         return ms, pushes, drift, evals
 
     out = {}

@@ -296,8 +296,10 @@ class Simulation:
         return self._h
 
 
-def _reports_to_dicts(arr, n):
-    return [arr[b].as_dict() for b in range(n)]
+def _reports_view(arr):
+    """The per-instance reports as a numpy structured array (no copy): field
+    access by name, e.g. reps[b]["status"], as for the single-problem dicts."""
+    return np.ctypeslib.as_array(arr)
 
 
 class Batch:
@@ -359,17 +361,17 @@ class Batch:
         self._check(lib().pic_batch_set_instance(self._h, int(b), _ptr(species, 0), _ptr(x, 0),
                                                  _ptr(u, 0), _ptr(w, 0), _ptr(A, 0), _ptr(U, 0)))
 
-    def start(self) -> list:
+    def start(self):
         reps = (Report * self.B)()
         self._check(lib().pic_batch_start(self._h, reps))
-        return _reports_to_dicts(reps, self.B)
+        return _reports_view(reps)
 
-    def step(self, tol) -> list:
+    def step(self, tol):
         """One step of every instance; per-instance reports (status included)."""
         reps = (Report * self.B)()
         rc = lib().pic_batch_step(self._h, float(tol), reps)
         self._check(rc, allow=(PIC_EINNER, PIC_EOUTER))
-        return _reports_to_dicts(reps, self.B)
+        return _reports_view(reps)
 
     def particles(self, b):
         npart = int(self.np_[b])

@@ -19,10 +19,11 @@
 //              in shared memory: FFT of the trial current, Nyquist projection
 //              (Eq. nyquist-projector), continuity and the per-mode CN update,
 //              inverse FFTs, and the gather records of the particle map;
-//   k_bmap     every particle of every instance: the particle map (inner
-//              Picard iteration, GM-HC push, orbit deposit) of map_device.cuh,
-//              each CTA reading its instance's geometry (one launch for plain
-//              evaluations, one for the final diagnostic pass);
+//   k_bmap     the particle map (inner Picard iteration, GM-HC push, orbit
+//              deposit) of map_device.cuh over the blocks of the instances
+//              that evaluate: k_bctl lists them, and a persistent grid walks
+//              the list, each block reading its instance's geometry (one
+//              launch for plain evaluations, one for the final pass);
 //   k_bresid   one CTA per instance: H = P J_orb, r = H - j, the sums of Eq.
 //              mixed-nonlinear-tests, the Gram products the next Anderson
 //              solve needs, and (final pass) the particle and mesh work.
@@ -31,8 +32,9 @@
 // instance evaluates (or at a round limit that Algorithm 1 cannot reach), so
 // the host waits once per step.  Instances that finished early skip the rest
 // of the rounds.  Where the driver cannot build that graph, the host launches
-// the rounds itself and reads the loop state after each.  Every instance then commits (or, on failure, keeps) its state
-// exactly as a single-problem context does (pic_step).
+// the rounds itself and reads the loop state after each.  Every instance
+// then commits (or, on failure, keeps) its state exactly as a single-problem
+// context does (pic_step).
 //
 // Per-instance initial states (pic_start) are prepared by a temporary
 // single-problem context per distinct grid and copied in.
@@ -98,6 +100,7 @@ struct BLoop {
   int running;   // instances that evaluate in the current round
   int rounds;    // rounds started in this step
   int overflow;  // the round limit was reached with instances still running
+  int nwork[2];  // particle-map blocks of this round: plain evaluations, final passes
   int pad;
 };
 
@@ -138,6 +141,8 @@ struct pic_batch {
   PGeom *d_pg;
   void *d_invdx;  // per instance (1/dx, 1/dV) in the particle type
   int32_t *d_blk2inst;
+  int32_t *d_work;  // per-round particle-map block lists (2 x nblocks)
+  int num_sms;
   BState *d_state, *h_state;  // h_state pinned
   BRes *d_res;
   EvalCounters *d_cnt;
@@ -348,8 +353,10 @@ __device__ void outer_top(BState &s, const BParams &bp) {
 __global__ void __launch_bounds__(kCtlThreads)
 k_bctl(int B, BState *__restrict__ states, const BRes *__restrict__ res,
        const EvalCounters *__restrict__ cnts, const BInst *__restrict__ inst, BParams bp,
-       BLoop *__restrict__ loop, int max_rounds, cudaGraphConditionalHandle cond) {
+       BLoop *__restrict__ loop, int max_rounds, cudaGraphConditionalHandle cond,
+       int32_t *__restrict__ work, int nblocks) {
   __shared__ int s_run;
+  __shared__ int s_cnt[2][kCtlThreads];
   if (threadIdx.x == 0) s_run = 0;
   __syncthreads();
   int run = 0;
@@ -475,6 +482,43 @@ k_bctl(int B, BState *__restrict__ states, const BRes *__restrict__ res,
     const bool more = s_run > 0 && r < max_rounds;
     if (s_run > 0 && !more) loop->overflow = 1;
     if (cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
+  // Work lists of this round's particle-map launches: the blocks of the
+  // instances that evaluate (list 0: plain evaluations, list 1: final
+  // passes), instances in order; each thread lists a contiguous run of
+  // instances at offsets from a scan of the counts.
+  const int chunk = (B + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int b0 = min(B, (int)threadIdx.x * chunk), b1 = min(B, b0 + chunk);
+  int c0 = 0, c1 = 0;
+  for (int b = b0; b < b1; b++) {
+    const int m = states[b].mode;
+    if (m == B_EVAL) c0 += inst[b].nblk;
+    else if (m == B_FINAL) c1 += inst[b].nblk;
+  }
+  s_cnt[0][threadIdx.x] = c0;
+  s_cnt[1][threadIdx.x] = c1;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {  // inclusive scan of both counts
+    const int a0 = (int)threadIdx.x >= o ? s_cnt[0][threadIdx.x - o] : 0;
+    const int a1 = (int)threadIdx.x >= o ? s_cnt[1][threadIdx.x - o] : 0;
+    __syncthreads();
+    s_cnt[0][threadIdx.x] += a0;
+    s_cnt[1][threadIdx.x] += a1;
+    __syncthreads();
+  }
+  int o0 = s_cnt[0][threadIdx.x] - c0, o1 = s_cnt[1][threadIdx.x] - c1;
+  for (int b = b0; b < b1; b++) {
+    const int m = states[b].mode;
+    if (m != B_EVAL && m != B_FINAL) continue;
+    const BInst in = inst[b];
+    int32_t *dst = m == B_EVAL ? work + o0 : work + nblocks + o1;
+    for (int k = 0; k < in.nblk; k++) dst[k] = in.blk0 + k;
+    if (m == B_EVAL) o0 += in.nblk;
+    else o1 += in.nblk;
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    loop->nwork[0] = s_cnt[0][threadIdx.x];
+    loop->nwork[1] = s_cnt[1][threadIdx.x];
   }
 }
 
@@ -675,19 +719,27 @@ __global__ void __launch_bounds__(kBT) k_bfield(BField p, T *__restrict__ nodes,
 template <typename T, bool FIN, bool GEN>
 __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 4 : 1)
 k_bmap(PView<T> pv, const int32_t *__restrict__ blk2inst, const BInst *__restrict__ inst,
-       const BState *__restrict__ st, const PGeom *__restrict__ pgs,
-       const T *__restrict__ invdx, KConst<T> kc, const T *__restrict__ nodes,
-       const T *__restrict__ nodes_u, double *__restrict__ Jorb, EvalCounters *__restrict__ cnt,
-       double *__restrict__ psum) {
-  const int b = blk2inst[blockIdx.x];
-  if (st[b].mode != (FIN ? B_FINAL : B_EVAL)) return;  // uniform over the CTA
-  const BInst in = inst[b];
-  pv.np = in.pend;
-  const MapScale<T> ms = {{invdx[2 * b], T(1), T(1)}, invdx[2 * b + 1]};
-  const PGeom pg = pgs[b];
-  map_block<1, T, FIN, GEN>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes + in.moff * 8,
-                            nodes_u + in.moff * 4, Jorb + 3 * in.moff, pg, kc, ms, cnt + b,
-                            psum);
+       const PGeom *__restrict__ pgs, const T *__restrict__ invdx, KConst<T> kc,
+       const T *__restrict__ nodes, const T *__restrict__ nodes_u, double *__restrict__ Jorb,
+       EvalCounters *__restrict__ cnt, double *__restrict__ psum,
+       const int32_t *__restrict__ work, const BLoop *__restrict__ loop, int nblocks) {
+  // a persistent grid walks this round's list of blocks (k_bctl): blocks of
+  // instances that do not evaluate in this mode cost nothing
+  const int nw = loop->nwork[FIN ? 1 : 0];
+  const int32_t *list = work + (FIN ? nblocks : 0);
+  for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    __syncthreads();  // the shared scratch of the previous block is free
+    const int blk = list[w];
+    const int b = blk2inst[blk];
+    const BInst in = inst[b];
+    PView<T> v = pv;
+    v.np = in.pend;
+    const MapScale<T> ms = {{invdx[2 * b], T(1), T(1)}, invdx[2 * b + 1]};
+    const PGeom pg = pgs[b];
+    map_block<1, T, FIN, GEN>(v, blk * (int64_t)kPT + threadIdx.x, nodes + in.moff * 8,
+                              nodes_u + in.moff * 4, Jorb + 3 * in.moff, pg, kc, ms, cnt + b,
+                              psum + 2 * (size_t)blk);
+  }
 }
 
 // H = P J_orb (the real-space Nyquist projector: in 1D, subtract the
@@ -1163,6 +1215,20 @@ size_t field_smem(const pic_batch *bt) {
 }
 
 // the kernels of one round (see the file comment)
+// persistent grid of a particle-map variant: every SM filled with as many
+// CTAs as it holds, never more CTAs than blocks
+template <typename T, bool FIN, bool GEN>
+int map_grid(pic_batch *bt) {
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bmap<T, FIN, GEN>, kPT, 0) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return std::max(1, std::min(bt->nblocks, per_sm * bt->num_sms));
+}
+
 // rounds a step may take: every round is one evaluation per running
 // instance, Algorithm 1 needs at most 2 + outer_max (2 levels + 1) of them,
 // and one more round finds no instance running
@@ -1176,7 +1242,8 @@ int enqueue_round(pic_batch *bt, double tr, double ta, double itr, double ita,
   const int B = bt->B;
   const BMesh m = b_mesh(bt);
   k_bctl<<<1, kCtlThreads, 0, bt->st>>>(B, bt->d_state, bt->d_res, bt->d_cnt, bt->d_inst,
-                                         b_params(bt, tr, ta), bt->d_loop, max_rounds(bt), cond);
+                                         b_params(bt, tr, ta), bt->d_loop, max_rounds(bt), cond,
+                                         bt->d_work, bt->nblocks);
   BKCHECK();
   k_baccept<<<B, kBT, 0, bt->st>>>(m);
   BKCHECK();
@@ -1211,9 +1278,10 @@ int enqueue_round(pic_batch *bt, double tr, double ta, double itr, double ita,
   if (bt->nblocks > 0) {
     const KConst<T> kc = b_kconst<T>(bt, itr, ita);
 #define B_MAP_LAUNCH(FIN, GEN)                                                                \
-  k_bmap<T, FIN, GEN><<<bt->nblocks, kPT, 0, bt->st>>>(                                       \
-      b_pview<T>(bt), bt->d_blk2inst, bt->d_inst, bt->d_state, bt->d_pg, (const T *)bt->d_invdx, \
-      kc, (const T *)bt->nodes, (const T *)bt->nodes_u, bt->Jorb, bt->d_cnt, bt->psum)
+  k_bmap<T, FIN, GEN><<<map_grid<T, FIN, GEN>(bt), kPT, 0, bt->st>>>(                         \
+      b_pview<T>(bt), bt->d_blk2inst, bt->d_inst, bt->d_pg, (const T *)bt->d_invdx, kc,         \
+      (const T *)bt->nodes, (const T *)bt->nodes_u, bt->Jorb, bt->d_cnt, bt->psum, bt->d_work,  \
+      bt->d_loop, bt->nblocks)
     if (bt->opt.order != 2 || bt->opt.refine_max > 0) {
       B_MAP_LAUNCH(false, true);
       BKCHECK();
@@ -1392,8 +1460,8 @@ int b_sort(pic_batch *bt) {
 
 void b_free_all(pic_batch *bt) {
   if (bt->loop_exec) cudaGraphExecDestroy(bt->loop_exec);
-  void *dev[] = {bt->d_inst, bt->d_pg, bt->d_invdx, bt->d_blk2inst, bt->d_state, bt->d_res,
-                 bt->d_cnt, bt->d_loop, bt->cell, bt->sp, bt->iters, bt->keys, bt->cnt_sort,
+  void *dev[] = {bt->d_inst, bt->d_pg, bt->d_invdx, bt->d_blk2inst, bt->d_work, bt->d_state,
+                 bt->d_res, bt->d_cnt, bt->d_loop, bt->cell, bt->sp, bt->iters, bt->keys, bt->cnt_sort,
                  bt->id, bt->slot, bt->off, bt->P, bt->Am, bt->v0, bt->vbar, bt->Pnew, bt->tmp_r,
                  bt->w, bt->psum, bt->phi_h, bt->psi_h, bt->rho_h, bt->A_h, bt->U_h, bt->phi1_h,
                  bt->psi1_h, bt->rho1_h, bt->A1_h, bt->U1_h, bt->A_real, bt->A1_real, bt->J_acc,
@@ -1465,6 +1533,13 @@ int pic_batch_init(pic_batch **out, int B, const int *n, const double *L, const 
     }
     bt->st = bt->own_st;
   }
+  {
+    int dev = 0;
+    bt->num_sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&bt->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      cudaGetLastError();
+  }
   // instance table: meshes back to back, particle ranges padded to kPT
   bt->inst.resize(B);
   bt->np.assign(np, np + B);
@@ -1523,6 +1598,7 @@ int pic_batch_init(pic_batch **out, int B, const int *n, const double *L, const 
       {(void **)&bt->d_pg, sizeof(PGeom) * B},
       {&bt->d_invdx, R * 2 * B},
       {(void **)&bt->d_blk2inst, sizeof(int32_t) * std::max(blk, 1)},
+      {(void **)&bt->d_work, sizeof(int32_t) * 2 * std::max(blk, 1)},
       {(void **)&bt->d_state, sizeof(BState) * B},
       {(void **)&bt->d_res, sizeof(BRes) * B},
       {(void **)&bt->d_cnt, sizeof(EvalCounters) * B},

@@ -843,6 +843,7 @@ struct PView {
   int32_t *iters;
 };
 
+// sums of NQ values over the CTA, written to out[0 .. NQ)
 template <int NQ>
 __device__ __forceinline__ void block_sums(double (&v)[NQ], double *out) {
   __shared__ double sh[NQ][kPT / 32];
@@ -857,7 +858,7 @@ __device__ __forceinline__ void block_sums(double (&v)[NQ], double *out) {
   if (threadIdx.x < NQ) {
     double s = 0.0;
     for (int w = 0; w < kPT / 32; w++) s += sh[threadIdx.x][w];
-    out[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
+    out[threadIdx.x] = s;
   }
 }
 
@@ -1106,32 +1107,71 @@ __device__ __noinline__ bool refine_particle(const PushConst<T> &pc0, const int 
 // Picard iteration, deposit, counters.  pv.np bounds the particles of this
 // CTA's problem (threads with i >= pv.np only join the warp and block
 // collectives), pg / nodes / nodes_u / J / kc / ms / cnt describe that
-// problem, and psum[blockIdx.x] receives the final-pass partial sums.
+// problem, and psum[0..2) receives the CTA's final-pass partial sums.
 // GEN = false is the common path, compiled for quadratic shapes without
 // refinement; GEN = true reads the shape degree from kc and compiles in the
 // refinement retry (kc.refine_max > 0).  Keeping both out of the common
 // path leaves it with no call and no per-point branch on the degree.
 template <int D, typename T, bool FINAL, bool GEN = false>
-__device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i,
+__device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i_slot,
                                           const T *__restrict__ nodes,
                                           const T *__restrict__ nodes_u, double *__restrict__ J,
                                           const PGeom &pg, const KConst<T> &kc,
                                           const MapScale<T> &ms,
                                           EvalCounters *__restrict__ cnt,
                                           double *__restrict__ psum) {
+  // Piece-count grouping: a warp walks as many orbit pieces as its slowest
+  // lane, and most orbits have one piece while a few cross one or two knot
+  // planes.  So the CTA's particles are reordered (stably) by the number of
+  // half-integer planes their start velocity would cross, predicted from
+  // the offset and v(p^n), and thread t takes the t-th of that order: the
+  // orbits that cross gather in few warps.  The order changes only which
+  // thread computes which particle.
+  __shared__ int s_perm[kPT];
+  __shared__ int s_wcnt[kPT / 32][4];
+  {
+    int cls = 3;  // empty slots go last
+    if (i_slot < pv.np) {
+      cls = 0;
+#pragma unroll
+      for (int l = 0; l < D; l++) {
+        const T u = pv.off[l * pv.cap + i_slot] +
+                    (kc.warm ? pv.vbar[l * pv.cap + i_slot] : pv.v0[l * pv.cap + i_slot]) *
+                        kc.dt * ms.inv_dx[l];
+        cls += (u >= T(0.5) || u < T(-0.5)) ? 1 : 0;
+      }
+      cls = cls < 2 ? cls : 2;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned mine = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const unsigned b = __ballot_sync(0xffffffffu, cls == c);
+      if (lane == 0) s_wcnt[wid][c] = __popc(b);
+      if (cls == c) mine = b;
+    }
+    __syncthreads();
+    int pos = __popc(mine & ((1u << lane) - 1u));
+    for (int c = 0; c < cls; c++)
+      for (int w = 0; w < kPT / 32; w++) pos += s_wcnt[w][c];
+    for (int w = 0; w < wid; w++) pos += s_wcnt[w][cls];
+    s_perm[pos] = threadIdx.x;
+    __syncthreads();
+  }
+  const int64_t i = i_slot - threadIdx.x + s_perm[threadIdx.x];
   const bool active = i < pv.np;
   double work = 0.0, chain = 0.0;
   int iters = 0, npieces = 0, refined = 0;
   unsigned int st = 0;
   // FP32 deposit window of this warp (see WarpWin): reference cell = the
-  // cell of the warp's first particle, columns zeroed by their lanes
+  // cell of lane 0's particle, columns zeroed by their lanes
   constexpr bool kWin = WarpWin<D>::kOn && sizeof(T) == 4;
   __shared__ T s_win[kWin ? (kPT / 32) * WarpWin<D>::NE * 32 : 1];
   T *win_warp = s_win + (size_t)(threadIdx.x >> 5) * WarpWin<D>::NE * 32;
   T *win_col = kWin ? win_warp + (threadIdx.x & 31) : nullptr;
   int ref[3] = {0, 0, 0};
   if (kWin) {
-    const int64_t i0 = i - (threadIdx.x & 31);  // the warp's first particle
+    const int64_t i0 = __shfl_sync(0xffffffffu, i, 0);  // lane 0's particle
     if (i0 < pv.np) {
 #pragma unroll
       for (int l = 0; l < D; l++) ref[l] = pv.cell[l * pv.cap + i0];
@@ -1251,7 +1291,7 @@ k_map(PView<T> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
       double *__restrict__ psum) {
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   map_block<D, T, FINAL, GEN>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes, nodes_u, J, pg,
-                              kc, ms, cnt, psum);
+                              kc, ms, cnt, psum + 2 * (size_t)blockIdx.x);
 }
 
 }  // namespace
