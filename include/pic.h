@@ -162,6 +162,20 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out);
 int pic_eval_map(pic_ctx *ctx, const double *j, double tol, double *H,
                  double *vbar, double *Pnew, int32_t *inner_counts, int on_device);
 
+/* One evaluation of the outer map and its directional derivative (a
+   Jacobian-vector product): H = H(j) as pic_eval_map computes it, and
+   dH = H'(j) dj.  The field step's tangent is its CN update of dj with zero
+   accepted state; the particle part is differentiated in forward mode
+   through the inner Picard fixed point, the knot-split orbit integrals, the
+   GM-HC push and the deposit.  For a Newton-Krylov outer solver in place of
+   the Picard/Anderson iteration of Algorithm 1 (the paper has no tangent).
+   j, dj, H, dH: 3*Ng; H or dH may be NULL.  Only FP64 contexts with
+   quadratic shapes, no refinement and the cold inner start (PIC_EARG
+   otherwise).  Allocates its scratch (about (dim + 15) * 16 bytes per
+   particle) for the call and frees it. */
+int pic_eval_map_jvp(pic_ctx *ctx, const double *j, const double *dj, double tol,
+                     double *H, double *dH, int on_device);
+
 int64_t pic_num_particles(const pic_ctx *ctx);
 
 /* Copy the accepted particle state out, in load order.  Any pointer may be NULL. */

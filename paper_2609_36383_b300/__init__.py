@@ -25,7 +25,7 @@ PIC_FP64, PIC_MIXED = 0, 1
 
 # every symbol include/pic.h declares (checked by the CPU test suite)
 EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
-           "pic_start", "pic_step", "pic_eval_map", "pic_num_particles", "pic_get_particles",
+           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_num_particles", "pic_get_particles",
            "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
            "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free",
            "pic_batch_init", "pic_batch_set_instance", "pic_batch_start", "pic_batch_step",
@@ -95,6 +95,7 @@ def lib():
         L.pic_start.argtypes = [_VP, C.POINTER(Report)]
         L.pic_step.argtypes = [_VP, C.c_double, C.POINTER(Report)]
         L.pic_eval_map.argtypes = [_VP, _VP, C.c_double, _VP, _VP, _VP, _VP, C.c_int]
+        L.pic_eval_map_jvp.argtypes = [_VP, _VP, _VP, C.c_double, _VP, _VP, C.c_int]
         L.pic_num_particles.restype = C.c_int64
         L.pic_num_particles.argtypes = [_VP]
         L.pic_get_particles.argtypes = [_VP, _VP, _VP, _VP, _VP, C.c_int]
@@ -242,6 +243,17 @@ class Simulation:
                                 _ptr(Pn, 0), _ptr(it, 0), 0)
         self._check(rc, allow=(PIC_EINNER,))
         return rc, H, vb.reshape(3, npart), Pn.reshape(3, npart), it
+
+    def eval_map_jvp(self, j, dj, tol):
+        """H(j) and the directional derivative H'(j) dj (host arrays)."""
+        j = np.ascontiguousarray(j, np.float64)
+        dj = np.ascontiguousarray(dj, np.float64)
+        H = np.zeros(3 * self.Ng)
+        dH = np.zeros(3 * self.Ng)
+        rc = lib().pic_eval_map_jvp(self._h, _ptr(j, 0), _ptr(dj, 0), float(tol), _ptr(H, 0),
+                                    _ptr(dH, 0), 0)
+        self._check(rc, allow=(PIC_EINNER,))
+        return rc, H, dH
 
     # -- state access ---------------------------------------------------------
     def num_particles(self) -> int:

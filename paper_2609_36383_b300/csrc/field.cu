@@ -407,6 +407,27 @@ int field_cn_update(pic_ctx *ctx, const double2 *jh, int want_uhalf) {
   return PIC_OK;
 }
 
+// The tangent of the field step in the direction jh: the CN update is
+// affine in the trial current, so its derivative is the same update with
+// the accepted state (phi, psi, rho, A, U) replaced by zero (`zero`: 3 Ng
+// zero modes).  The candidate n+1 buffers receive the tangents.
+int field_cn_update_tangent(pic_ctx *ctx, const double2 *jh, const double2 *zero) {
+  CnArgs p;
+  p.jh = jh;
+  p.rho = zero; p.phi = zero; p.psi = zero; p.A = zero; p.U = zero;
+  p.rho1 = ctx->rho1_h; p.phi1 = ctx->phi1_h; p.psi1 = ctx->psi1_h; p.A1 = ctx->A1_h;
+  p.U1 = ctx->U1_h;
+  p.out = ctx->work_h;
+  p.dt = ctx->dt;
+  p.kap2 = ctx->opt.kappa * ctx->opt.kappa;
+  p.sigma1 = ctx->opt.sigma1;
+  p.sigma2 = ctx->opt.sigma2;
+  p.want_uhalf = 0;
+  k_cn_update<<<blocks(ctx->g.Ng), kThreads, 0, ctx->st>>>(p, spec_geom(ctx));
+  KCHECK();
+  return PIC_OK;
+}
+
 int field_pack_nodes(pic_ctx *ctx, int want_uhalf) {
   const int d = ctx->g.dim, Ng = ctx->g.Ng;
   int nc = d + 3 + (want_uhalf ? 3 : 0);

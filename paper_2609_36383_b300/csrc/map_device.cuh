@@ -25,6 +25,7 @@
 // frame, so the FP32 instantiation keeps its resolution anywhere in the box.
 #pragma once
 
+#include "dual.cuh"
 #include "pic_internal.cuh"
 
 #include <cmath>
@@ -114,6 +115,20 @@ KConst<T> kconst(const StepConst &sc, const PGeom &pg) {
 // For FP32 the conversion is done with integer operations (sign, exponent
 // rebias by 1023 - 127 = 896, mantissa shift by 29) so that it does not
 // occupy the narrow FP64 pipe; FP32 subnormals (< 1.2e-38) flush to zero.
+// Deposit of one contribution into the FP64 current J (3 Ng values); a Dual
+// contribution also deposits its tangent into the array that follows J.
+__device__ __forceinline__ void dep_add(double *J, size_t idx, size_t, double v) {
+  atomicAdd(J + idx, v);
+}
+__device__ __forceinline__ double widen(float v);
+__device__ __forceinline__ void dep_add(double *J, size_t idx, size_t, float v) {
+  atomicAdd(J + idx, widen(v));
+}
+__device__ __forceinline__ void dep_add(double *J, size_t idx, size_t span, const Dual &v) {
+  atomicAdd(J + idx, v.v);
+  atomicAdd(J + span + idx, v.d);
+}
+
 __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ double widen(float v) {
   const unsigned u = __float_as_uint(v);
@@ -267,6 +282,15 @@ __device__ __forceinline__ void load_rec(const double *__restrict__ p, double (&
     double2 v = __ldg(reinterpret_cast<const double2 *>(p) + k);
     o[2 * k] = v.x;
     o[2 * k + 1] = v.y;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void load_rec(const Dual *__restrict__ p, Dual (&o)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; k++) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + k);
+    o[k] = Dual(v.x, v.y);
   }
 }
 
@@ -593,7 +617,7 @@ struct DepositOrbit {
             }
 #pragma unroll
             for (int c = 0; c < 3; c++)
-              atomicAdd(J + (size_t)c * pg->Ng + g, widen(qv[c] * pa.Sb[k]));
+              dep_add(J, (size_t)c * pg->Ng + g, 3 * (size_t)pg->Ng, qv[c] * pa.Sb[k]);
           }
       }
       return;
@@ -642,7 +666,7 @@ struct DepositOrbit {
           for (int c = 0; c < 3; c++) {
             const T v = qv[c] * pa.Sb[k];
             if (e >= 0) win[(e + c) * 32] += v;
-            else atomicAdd(J + (size_t)c * pg->Ng + g, widen(v));
+            else dep_add(J, (size_t)c * pg->Ng + g, 3 * (size_t)pg->Ng, v);
           }
         }
   }
@@ -862,6 +886,24 @@ __device__ __forceinline__ void block_sums(double (&v)[NQ], double *out) {
   }
 }
 
+// The inner test on the tangent of a Dual iteration (the tangent iteration
+// converges at the rate of the value's; it passes when its change meets the
+// same mixed test); values of plain types have no tangent.
+template <typename T>
+__device__ __forceinline__ bool tangent_settled(const T *, const T *, T, T) {
+  return true;
+}
+__device__ __forceinline__ bool tangent_settled(const Dual *vn, const Dual *vb, Dual tau_a,
+                                                Dual tau_r) {
+  double gap = 0.0, nrm = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    gap = fmax(gap, ::fabs(vn[c].d - vb[c].d));
+    nrm = fmax(nrm, ::fabs(vn[c].d));
+  }
+  return gap <= tau_a.v + tau_r.v * nrm;
+}
+
 // One particle's inner Picard iteration (Sec. 4.5, reading R6) over the
 // straight orbit that starts at (cell, off) and lasts tsp of the field step
 // (tsp = 1 unless SUB: then the orbit is the substep [ta, ta + tsp] of a
@@ -930,12 +972,13 @@ __device__ __forceinline__ bool picard(const PushConst<T> &pc, const int cell[3]
       sl |= PIC_ST_SUPERLUM;
       break;
     }
+    const bool tan_ok = tangent_settled(vn, vb, tau_a, tau_r);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       vb[c] = vn[c];
       Pn1[c] = Pc[c];
     }
-    if (diff <= tau_a + tau_r * nrm) {
+    if (diff <= tau_a + tau_r * nrm && tan_ok) {
       conv = true;
       break;
     }
@@ -1170,7 +1213,7 @@ __device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i_sl
   T *win_warp = s_win + (size_t)(threadIdx.x >> 5) * WarpWin<D>::NE * 32;
   T *win_col = kWin ? win_warp + (threadIdx.x & 31) : nullptr;
   int ref[3] = {0, 0, 0};
-  if (kWin) {
+  if constexpr (kWin) {
     const int64_t i0 = __shfl_sync(0xffffffffu, i, 0);  // lane 0's particle
     if (i0 < pv.np) {
 #pragma unroll
@@ -1244,7 +1287,7 @@ __device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i_sl
     }
     pv.iters[i] = iters;
   }
-  if (kWin) {
+  if constexpr (kWin) {
     // reduce the 32 columns of the warp window (rotated so that the lanes read
     // 32 different banks) and flush each touched entry with one FP64 atomic
     __syncwarp();

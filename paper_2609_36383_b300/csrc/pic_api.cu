@@ -109,6 +109,8 @@ int alloc_mesh(pic_ctx *ctx) {
   return PIC_OK;
 }
 
+}  // namespace
+
 // effective tolerances (reading R9 for the mixed path)
 void tolerances(const pic_ctx *ctx, double tol, double *tr, double *ta, double *itr,
                 double *ita) {
@@ -141,6 +143,8 @@ StepConst make_sc(const pic_ctx *ctx, double itr, double ita) {
   gauss_legendre01(sc.ngl, sc.gl_t, sc.gl_w);
   return sc;
 }
+
+namespace {
 
 struct Eval {
   EvalCounters cnt;

@@ -148,6 +148,12 @@ struct pic_ctx {
 // Gauss-Legendre nodes t and weights w of an n-point rule on [0, 1]
 void gauss_legendre01(int n, double *t, double *w);
 
+// outer and inner tolerances of a step at tolerance tol (reading R9), and
+// the particle-map constants built from the inner ones
+void tolerances(const pic_ctx *ctx, double tol, double *tr, double *ta, double *itr,
+                double *ita);
+StepConst make_sc(const pic_ctx *ctx, double itr, double ita);
+
 // drop every captured graph (buffers or sizes changed)
 void graphs_clear(pic_ctx *ctx);
 
@@ -181,6 +187,8 @@ int field_complex_to_real(pic_ctx *ctx, const double2 *src, double *dst, int nco
 int field_project_h(pic_ctx *ctx, double2 *f, int ncomp);
 int field_cn_update(pic_ctx *ctx, const double2 *jh, int want_uhalf);
 int field_pack_nodes(pic_ctx *ctx, int want_uhalf);
+// tangent of the CN update in the direction jh (zero accepted state)
+int field_cn_update_tangent(pic_ctx *ctx, const double2 *jh, const double2 *zero);
 int field_initial_constraints(pic_ctx *ctx);
 int field_energy(pic_ctx *ctx, const double2 *phi_h, const double2 *A_h,
                  const double2 *U_h, double *W);
