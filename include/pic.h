@@ -176,6 +176,41 @@ int pic_eval_map(pic_ctx *ctx, const double *j, double tol, double *H,
 int pic_eval_map_jvp(pic_ctx *ctx, const double *j, const double *dj, double tol,
                      double *H, double *dH, int on_device);
 
+/* Forward sensitivity of the whole step (the tangent of the state with
+   respect to one parameter of the initial condition), for gradients of
+   quantities after many steps.  pic_tangent_begin seeds it at the started
+   state: du, the tangent of the particles' mechanical u (3*N, load order),
+   and dA, dU, the tangents of the initial potentials (3*Ng each); any may
+   be NULL (zero).  The positions carry no seed.  The seed follows pic_start:
+   dA and dU are projected, dP = m du + q (P dA)_h(x), dphi from Gauss's law,
+   dpsi from the Lorenz gauge, drho = 0.  From then on every successful
+   pic_step also advances the tangent: the tangent dj of the converged
+   current solves (I - H_j) dj = H_s dS (implicit differentiation of the
+   fixed point j = H(j; S) of Sec. 4.5 with respect to the accepted state S)
+   by restarted GMRES(20) on JVPs until |dj - H_j dj - H_S dS| is at most
+   max(tol, 1e-12) times the larger of |dj| and |H_S dS| (or stalls below
+   1e-9 of it: the attainable accuracy where the net tangent current is a
+   small part of its gross terms);
+   the tangents of vbar, P^{n+1} and the CN field step follow from dj.  A
+   tangent solve that does not converge fails the step with PIC_EOUTER and
+   leaves state and tangent unchanged.  FP64 contexts with quadratic shapes,
+   no refinement and the cold inner start only (PIC_EARG otherwise).
+   Allocates about (dim + 3) * 8 + (dim + 15) * 16 bytes per particle and
+   about 1.4 kB per mesh node; pic_tangent_end (or pic_start,
+   pic_set_particles, pic_set_state, pic_free) releases it. */
+int pic_tangent_begin(pic_ctx *ctx, const double *du, const double *dA, const double *dU,
+                      int on_device);
+int pic_tangent_end(pic_ctx *ctx);
+
+/* The tangent of the accepted state: dx (dim*N, physical units) and dP
+   (3*N) in load order, dA, dU (3*Ng, real space), and the tangents of the
+   kinetic, field and total energy (dK, dW; their sum is conserved exactly
+   as E_tot is).  Any pointer may be NULL.  PIC_ESTATE without a tangent.
+   gmres_iters (may be NULL) receives the Krylov iterations of the last
+   step's tangent solve. */
+int pic_get_tangent(pic_ctx *ctx, double *dx, double *dP, double *dA, double *dU, double *dK,
+                    double *dW, int *gmres_iters, int on_device);
+
 int64_t pic_num_particles(const pic_ctx *ctx);
 
 /* Copy the accepted particle state out, in load order.  Any pointer may be NULL. */

@@ -25,7 +25,8 @@ PIC_FP64, PIC_MIXED = 0, 1
 
 # every symbol include/pic.h declares (checked by the CPU test suite)
 EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
-           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_num_particles", "pic_get_particles",
+           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp",
+           "pic_tangent_begin", "pic_tangent_end", "pic_get_tangent", "pic_num_particles", "pic_get_particles",
            "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
            "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free",
            "pic_batch_init", "pic_batch_set_instance", "pic_batch_start", "pic_batch_step",
@@ -96,6 +97,9 @@ def lib():
         L.pic_step.argtypes = [_VP, C.c_double, C.POINTER(Report)]
         L.pic_eval_map.argtypes = [_VP, _VP, C.c_double, _VP, _VP, _VP, _VP, C.c_int]
         L.pic_eval_map_jvp.argtypes = [_VP, _VP, _VP, C.c_double, _VP, _VP, C.c_int]
+        L.pic_tangent_begin.argtypes = [_VP, _VP, _VP, _VP, C.c_int]
+        L.pic_tangent_end.argtypes = [_VP]
+        L.pic_get_tangent.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int]
         L.pic_num_particles.restype = C.c_int64
         L.pic_num_particles.argtypes = [_VP]
         L.pic_get_particles.argtypes = [_VP, _VP, _VP, _VP, _VP, C.c_int]
@@ -254,6 +258,29 @@ class Simulation:
                                     _ptr(dH, 0), 0)
         self._check(rc, allow=(PIC_EINNER,))
         return rc, H, dH
+
+    def tangent_begin(self, du=None, dA=None, dU=None):
+        """Seed the forward sensitivity at the started state: du (3, N) in load
+        order, dA and dU (3 * Ng); None = zero.  Every later step advances it."""
+        arrs = [None if a is None else np.ascontiguousarray(a, np.float64).ravel()
+                for a in (du, dA, dU)]
+        self._check(lib().pic_tangent_begin(self._h, *[_ptr(a, 0) for a in arrs], 0))
+
+    def tangent_end(self):
+        self._check(lib().pic_tangent_end(self._h))
+
+    def tangent(self) -> dict:
+        """The tangent of the accepted state: dx (dim, N), dP (3, N) in load
+        order, dA, dU (3 * Ng), dK, dW and the last step's GMRES iterations."""
+        n = self.num_particles()
+        dx = np.zeros(self.dim * n); dP = np.zeros(3 * n)
+        dA = np.zeros(3 * self.Ng); dU = np.zeros(3 * self.Ng)
+        dK = C.c_double(); dW = C.c_double(); it = C.c_int()
+        self._check(lib().pic_get_tangent(self._h, _ptr(dx, 0), _ptr(dP, 0), _ptr(dA, 0),
+                                          _ptr(dU, 0), C.byref(dK), C.byref(dW), C.byref(it),
+                                          0))
+        return dict(dx=dx.reshape(self.dim, n), dP=dP.reshape(3, n), dA=dA, dU=dU,
+                    dK=dK.value, dW=dW.value, gmres_iters=it.value)
 
     # -- state access ---------------------------------------------------------
     def num_particles(self) -> int:

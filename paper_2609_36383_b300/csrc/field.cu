@@ -239,6 +239,37 @@ __global__ void k_energy_parts(const double2 *phi, const double2 *A, const doubl
   block_sum_write<1>(v, out);
 }
 
+// Tangent of the field energy density: the derivative of |E|^2 / (2 sigma1)
+// + |B|^2 / (2 sigma2) in the direction (dphi, dA, dU) is
+// Re(conj(E) dE) / sigma1 + Re(conj(B) dB) / sigma2, with dE and dB the same
+// linear maps of the tangent.
+__global__ void k_energy_tangent_parts(const double2 *phi, const double2 *A, const double2 *U,
+                                       const double2 *dphi, const double2 *dA,
+                                       const double2 *dU, SpecGeom sg, double inv_2s1,
+                                       double inv_2s2, double *out) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (g < sg.Ng) {
+    const int Ng = sg.Ng;
+    double k[3];
+    mode_symbols(sg, g, k);
+    const double2 ph = phi[g], dph = dphi[g];
+    double e2 = 0.0, b2 = 0.0;
+    for (int c = 0; c < 3; c++) {
+      const double2 E = cadd(cmul_i(-k[c], ph), cscale(-1.0, U[c * Ng + g]));
+      const double2 dE = cadd(cmul_i(-k[c], dph), cscale(-1.0, dU[c * Ng + g]));
+      e2 += E.x * dE.x + E.y * dE.y;
+      const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+      const double2 B = cadd(cmul_i(k[c1], A[c2 * Ng + g]), cmul_i(-k[c2], A[c1 * Ng + g]));
+      const double2 dB =
+          cadd(cmul_i(k[c1], dA[c2 * Ng + g]), cmul_i(-k[c2], dA[c1 * Ng + g]));
+      b2 += B.x * dB.x + B.y * dB.y;
+    }
+    v[0] = 2.0 * (e2 * inv_2s1 + b2 * inv_2s2);
+  }
+  block_sum_write<1>(v, out);
+}
+
 __global__ void k_constraint_parts(const double2 *phi, const double2 *psi, const double2 *rho,
                                    const double2 *A, const double2 *U, SpecGeom sg,
                                    double sigma1, double inv_kap2, double *out) {
@@ -390,13 +421,13 @@ int field_project_h(pic_ctx *ctx, double2 *f, int ncomp) {
   return PIC_OK;
 }
 
-int field_cn_update(pic_ctx *ctx, const double2 *jh, int want_uhalf) {
+int field_cn_update_into(pic_ctx *ctx, const double2 *jh, const SpecState &in,
+                         const SpecState &out, double2 *spec, int want_uhalf) {
   CnArgs p;
   p.jh = jh;
-  p.rho = ctx->rho_h; p.phi = ctx->phi_h; p.psi = ctx->psi_h; p.A = ctx->A_h; p.U = ctx->U_h;
-  p.rho1 = ctx->rho1_h; p.phi1 = ctx->phi1_h; p.psi1 = ctx->psi1_h; p.A1 = ctx->A1_h;
-  p.U1 = ctx->U1_h;
-  p.out = ctx->work_h;
+  p.rho = in.rho; p.phi = in.phi; p.psi = in.psi; p.A = in.A; p.U = in.U;
+  p.rho1 = out.rho; p.phi1 = out.phi; p.psi1 = out.psi; p.A1 = out.A; p.U1 = out.U;
+  p.out = spec;
   p.dt = ctx->dt;
   p.kap2 = ctx->opt.kappa * ctx->opt.kappa;
   p.sigma1 = ctx->opt.sigma1;
@@ -407,25 +438,10 @@ int field_cn_update(pic_ctx *ctx, const double2 *jh, int want_uhalf) {
   return PIC_OK;
 }
 
-// The tangent of the field step in the direction jh: the CN update is
-// affine in the trial current, so its derivative is the same update with
-// the accepted state (phi, psi, rho, A, U) replaced by zero (`zero`: 3 Ng
-// zero modes).  The candidate n+1 buffers receive the tangents.
-int field_cn_update_tangent(pic_ctx *ctx, const double2 *jh, const double2 *zero) {
-  CnArgs p;
-  p.jh = jh;
-  p.rho = zero; p.phi = zero; p.psi = zero; p.A = zero; p.U = zero;
-  p.rho1 = ctx->rho1_h; p.phi1 = ctx->phi1_h; p.psi1 = ctx->psi1_h; p.A1 = ctx->A1_h;
-  p.U1 = ctx->U1_h;
-  p.out = ctx->work_h;
-  p.dt = ctx->dt;
-  p.kap2 = ctx->opt.kappa * ctx->opt.kappa;
-  p.sigma1 = ctx->opt.sigma1;
-  p.sigma2 = ctx->opt.sigma2;
-  p.want_uhalf = 0;
-  k_cn_update<<<blocks(ctx->g.Ng), kThreads, 0, ctx->st>>>(p, spec_geom(ctx));
-  KCHECK();
-  return PIC_OK;
+int field_cn_update(pic_ctx *ctx, const double2 *jh, int want_uhalf) {
+  const SpecState in = {ctx->rho_h, ctx->phi_h, ctx->psi_h, ctx->A_h, ctx->U_h};
+  const SpecState out = {ctx->rho1_h, ctx->phi1_h, ctx->psi1_h, ctx->A1_h, ctx->U1_h};
+  return field_cn_update_into(ctx, jh, in, out, ctx->work_h, want_uhalf);
 }
 
 int field_pack_nodes(pic_ctx *ctx, int want_uhalf) {
@@ -443,6 +459,38 @@ int field_pack_nodes(pic_ctx *ctx, int want_uhalf) {
         ctx->work_h, ctx->A_real, ctx->A1_real, (float *)ctx->nodes, (float *)ctx->nodes_u, Ng, d,
         node_record_len(d), inv, want_uhalf);
   KCHECK();
+  return PIC_OK;
+}
+
+int field_pack_nodes_into(pic_ctx *ctx, double2 *spec, const double *A_n, double *A1_real,
+                          double *nodes) {
+  const int d = ctx->g.dim, Ng = ctx->g.Ng;
+  int st = fft_nd(ctx, spec, d + 3, +1);
+  if (st) return st;
+  k_pack_nodes<double><<<blocks(Ng), kThreads, 0, ctx->st>>>(
+      spec, A_n, A1_real, nodes, nullptr, Ng, d, node_record_len(d), 1.0 / Ng, 0);
+  KCHECK();
+  return PIC_OK;
+}
+
+int field_initial_constraints_into(pic_ctx *ctx, const SpecState &f) {
+  k_initial_constraints<<<blocks(ctx->g.Ng), kThreads, 0, ctx->st>>>(
+      f.phi, f.psi, f.rho, f.A, f.U, spec_geom(ctx), ctx->opt.sigma1,
+      ctx->opt.kappa * ctx->opt.kappa);
+  KCHECK();
+  return PIC_OK;
+}
+
+int field_energy_tangent(pic_ctx *ctx, const SpecState &f, const SpecState &df, double *dW) {
+  int nb = blocks(ctx->g.Ng);
+  k_energy_tangent_parts<<<nb, kThreads, 0, ctx->st>>>(f.phi, f.A, f.U, df.phi, df.A, df.U,
+                                                       spec_geom(ctx), 0.5 / ctx->opt.sigma1,
+                                                       0.5 / ctx->opt.sigma2, ctx->red);
+  KCHECK();
+  double s;
+  int e = finish_sum<1>(ctx, nb, &s);
+  if (e) return e;
+  *dW = s * ctx->g.dV / ctx->g.Ng;
   return PIC_OK;
 }
 

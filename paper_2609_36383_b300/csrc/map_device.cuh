@@ -886,23 +886,15 @@ __device__ __forceinline__ void block_sums(double (&v)[NQ], double *out) {
   }
 }
 
-// The inner test on the tangent of a Dual iteration (the tangent iteration
-// converges at the rate of the value's; it passes when its change meets the
-// same mixed test); values of plain types have no tangent.
+// Extra inner sweeps after the value has passed the inner test: none for
+// plain types; two for dual numbers, whose tangent converges at the value's
+// rate and so is still about as far from its fixed point as the value was.
+// The count depends on the value alone, so a dual map evaluation is exactly
+// linear in its tangent inputs (the branches of the value decide everything).
 template <typename T>
-__device__ __forceinline__ bool tangent_settled(const T *, const T *, T, T) {
-  return true;
-}
-__device__ __forceinline__ bool tangent_settled(const Dual *vn, const Dual *vb, Dual tau_a,
-                                                Dual tau_r) {
-  double gap = 0.0, nrm = 0.0;
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    gap = fmax(gap, ::fabs(vn[c].d - vb[c].d));
-    nrm = fmax(nrm, ::fabs(vn[c].d));
-  }
-  return gap <= tau_a.v + tau_r.v * nrm;
-}
+constexpr int kTangentSweeps = 0;
+template <>
+constexpr int kTangentSweeps<Dual> = 2;
 
 // One particle's inner Picard iteration (Sec. 4.5, reading R6) over the
 // straight orbit that starts at (cell, off) and lasts tsp of the field step
@@ -919,9 +911,9 @@ __device__ __forceinline__ bool picard(const PushConst<T> &pc, const int cell[3]
   const T tau_r = kc.tau_r, tau_a = kc.tau_a, kap2 = kc.kappa * kc.kappa;
   unsigned int sl = 0;
   bool conv = false;
-  int it;
+  int it, extra = -1;  // sweeps left after the value converged (dual numbers)
 #pragma unroll 1
-  for (it = 1; it <= kc.inner_max; it++) {
+  for (it = 1; it <= kc.inner_max + kTangentSweeps<T>; it++) {
     GatherOrbit<D, T, SUB> go;
     go.nodes = nodes;
     go.pg = &pg;
@@ -972,15 +964,24 @@ __device__ __forceinline__ bool picard(const PushConst<T> &pc, const int cell[3]
       sl |= PIC_ST_SUPERLUM;
       break;
     }
-    const bool tan_ok = tangent_settled(vn, vb, tau_a, tau_r);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       vb[c] = vn[c];
       Pn1[c] = Pc[c];
     }
-    if (diff <= tau_a + tau_r * nrm && tan_ok) {
-      conv = true;
-      break;
+    if constexpr (kTangentSweeps<T> == 0) {
+      if (diff <= tau_a + tau_r * nrm) {
+        conv = true;
+        break;
+      }
+    } else {
+      if (extra < 0 && it <= kc.inner_max && diff <= tau_a + tau_r * nrm)
+        extra = kTangentSweeps<T>;
+      if (extra == 0) {
+        conv = true;
+        break;
+      }
+      if (extra > 0) extra--;
     }
   }
   if (!conv && sl == 0) sl |= PIC_ST_NOCONV;

@@ -666,6 +666,10 @@ int particles_sort(pic_ctx *ctx) {
     if ((e = permute_field<float>(ctx, (float *)ctx->off, g.dim))) return e;
     if ((e = permute_field<float>(ctx, (float *)ctx->P, 3))) return e;
   }
+  if (ctx->tan) {  // the forward sensitivity travels with its particles
+    if ((e = permute_field<double>(ctx, ctx->tan->off, g.dim))) return e;
+    if ((e = permute_field<double>(ctx, ctx->tan->P, 3))) return e;
+  }
   if ((e = permute_field<double>(ctx, ctx->w, 1))) return e;
   if ((e = permute_field<int32_t>(ctx, ctx->sp, 1))) return e;
   if ((e = permute_field<int64_t>(ctx, ctx->id, 1))) return e;

@@ -54,6 +54,7 @@ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 int ilog2(int n) { int l = 0; while ((1 << l) < n) l++; return l; }
 
 void free_all(pic_ctx *ctx) {
+  tangent_free(ctx);
   void *ptrs[] = {ctx->cell, ctx->off, ctx->P, ctx->w, ctx->sp, ctx->id, ctx->Am, ctx->v0,
                   ctx->vbar, ctx->Pnew, ctx->iters, ctx->u_in, ctx->tmp_d, ctx->tmp_i, ctx->psum,
                   ctx->phi_h, ctx->psi_h, ctx->rho_h, ctx->A_h, ctx->U_h, ctx->A_real, ctx->J_acc,
@@ -465,6 +466,7 @@ int64_t pic_num_particles(const pic_ctx *ctx) { return ctx ? ctx->np : -1; }
 
 int pic_set_particles(pic_ctx *ctx, int64_t n, const int32_t *species, const double *x,
                       const double *u_or_P, int is_canonical, const double *w, int on_device) {
+  tangent_free(ctx);  // its arrays follow the particle storage
   if (!ctx) return PIC_EARG;
   if (n < 0 || (n > 0 && (!x || !u_or_P || !w))) {
     ctx->err = "pic_set_particles: bad arguments";
@@ -502,6 +504,7 @@ int pic_set_potentials(pic_ctx *ctx, const double *A, const double *U, int on_de
 
 int pic_start(pic_ctx *ctx, pic_report *out) {
   if (!ctx) return PIC_EARG;
+  tangent_free(ctx);
   const int Ng = ctx->g.Ng;
   int e;
   // project A and U (Sec. 4.5) and bring A back to real space
@@ -695,6 +698,11 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
     status = PIC_EOUTER;
     ctx->err = "outer iteration limit reached";
   }
+  // the forward sensitivity of the converged step (before anything commits)
+  if (status == PIC_OK && ctx->tan) {
+    status = tangent_solve(ctx, sc, tol);
+    if (status != PIC_OK && status != PIC_EOUTER && status != PIC_EINNER) return status;
+  }
   // keep the device buffers in their named slots for the next step
   ctx->j = j; ctx->H = H; ctx->r = r; ctx->jt = jt; ctx->Ht = Ht; ctx->rt = rt;
   if (status == PIC_OK) {
@@ -706,6 +714,7 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
     R.inner_mean = ctx->np ? (double)ev.cnt.inner_sum / ctx->np : 0.0;
     R.refined = (int)ev.cnt.refined;
     if ((e = particles_commit(ctx))) return e;
+    if (ctx->tan && (e = tangent_commit(ctx))) return e;
     std::swap(ctx->phi_h, ctx->phi1_h);
     std::swap(ctx->psi_h, ctx->psi1_h);
     std::swap(ctx->rho_h, ctx->rho1_h);

@@ -53,6 +53,32 @@ struct EvalCounters {
   unsigned long long refined;  // particles solved with substeps
 };
 
+// The spectral field state (accepted, candidate, or a tangent of either).
+struct SpecState {
+  double2 *rho, *phi, *psi, *A, *U;  // Ng, Ng, Ng, 3Ng, 3Ng modes
+};
+
+// Forward sensitivity of the state (pic_tangent_begin): the tangents of the
+// particle offsets and canonical momenta in slot order, of the spectral
+// field state, and the scratch of the tangent solve of one step.
+struct TangentState {
+  double *off;           // [dim][cap] tangent of the offset, node units
+  double *P;             // [3][cap]
+  SpecState f, f1;       // accepted and candidate field tangents
+  double *A_real;        // 3Ng tangent of A^n in real space
+  double *A1_real;       // 3Ng tangent of A^{n+1} of the last tangent evaluation
+  double2 *jh;           // 3Ng transform of the tangent trial current
+  double2 *work;         // (dim + 3) Ng tangent gather spectra
+  double *rec;           // Ng * nvp tangent gather records
+  void *drec;            // Ng * nvp dual records
+  void *dpart;           // (dim + 15) * cap dual particle arrays
+  double *Jd;            // 6Ng orbit current and its tangent
+  double *V;             // 21 * 3Ng Krylov basis
+  double *x, *b, *w, *Tx;  // 3Ng each
+  int gmres_iters;       // Krylov iterations of the last tangent solve
+  void *block;           // the single allocation behind all of the above
+};
+
 // Reduction partials returned to the host after the residual kernel.
 struct ResidSums {
   double r2, H2, j2, smax;
@@ -143,6 +169,7 @@ struct pic_ctx {
   GraphEntry graphs[16];
   int ngraphs;
   int graphs_off;  // capture failed once: launch directly
+  TangentState *tan;  // forward sensitivity, or null
 };
 
 // Gauss-Legendre nodes t and weights w of an n-point rule on [0, 1]
@@ -187,9 +214,20 @@ int field_complex_to_real(pic_ctx *ctx, const double2 *src, double *dst, int nco
 int field_project_h(pic_ctx *ctx, double2 *f, int ncomp);
 int field_cn_update(pic_ctx *ctx, const double2 *jh, int want_uhalf);
 int field_pack_nodes(pic_ctx *ctx, int want_uhalf);
-// tangent of the CN update in the direction jh (zero accepted state)
-int field_cn_update_tangent(pic_ctx *ctx, const double2 *jh, const double2 *zero);
 int field_initial_constraints(pic_ctx *ctx);
+// The CN update from any field state `in` into `out` and the gather spectra
+// `spec`; the update is linear in (j, state) jointly, so a tangent state and a
+// tangent current give the tangent of the field step.
+int field_cn_update_into(pic_ctx *ctx, const double2 *jh, const SpecState &in,
+                         const SpecState &out, double2 *spec, int want_uhalf);
+// FP64 gather records from the gather spectra `spec` (inverse-transformed in
+// place) and A^n in real space; A^{n+1} in real space goes to A1_real
+int field_pack_nodes_into(pic_ctx *ctx, double2 *spec, const double *A_n, double *A1_real,
+                          double *nodes);
+// phi from Gauss's law and psi from the Lorenz gauge of the state st
+int field_initial_constraints_into(pic_ctx *ctx, const SpecState &st);
+// tangent of the field energy: dW = sum d W / d(phi, A, U) . (dphi, dA, dU)
+int field_energy_tangent(pic_ctx *ctx, const SpecState &st, const SpecState &dst, double *dW);
 int field_energy(pic_ctx *ctx, const double2 *phi_h, const double2 *A_h,
                  const double2 *U_h, double *W);
 int field_constraints(pic_ctx *ctx, double *gauss_rms, double *lorenz_rms);
@@ -219,6 +257,13 @@ int particles_export_eval(pic_ctx *ctx, double *vbar, double *Pnew, int32_t *ite
                           int on_device);
 int particles_export_u(pic_ctx *ctx, double *u, int on_device);
 int particles_sort(pic_ctx *ctx);
+
+// ---------------------------------------------------------------- tangent.cu
+// advance the tangent through the converged step (before the commit) and
+// commit it (after the state's commit); free it
+int tangent_solve(pic_ctx *ctx, const StepConst &sc, double tol);
+int tangent_commit(pic_ctx *ctx);
+void tangent_free(pic_ctx *ctx);
 
 // ---------------------------------------------------------------- reduce.cu
 // queue r = H - j and its test sums (copied to pinned host memory);

@@ -1,0 +1,74 @@
+"""The torch.autograd wrappers (paper_2609_36383_b300.autograd) marshal the
+library's derivatives correctly: checked on the CPU against a stand-in
+simulation whose map is affine and whose energies are closed forms, so that
+torch's own forward and reverse modes have exact answers."""
+import numpy as np
+import pytest
+import torch
+import torch.autograd.forward_ad as fwAD
+
+from paper_2609_36383_b300 import autograd as pa
+
+
+class _AffineMap:
+    """H(j) = M j + c, with the JVP M dj."""
+
+    def __init__(self, n=12, seed=0):
+        rng = np.random.default_rng(seed)
+        self.M = rng.standard_normal((n, n))
+        self.c = rng.standard_normal(n)
+
+    def eval_map(self, j, tol):
+        return 0, self.M @ j + self.c, None, None, None
+
+    def eval_map_jvp(self, j, dj, tol):
+        return 0, self.M @ j + self.c, self.M @ dj
+
+
+class _Run:
+    """W(theta) = theta^3, K(theta) = sin(theta) after any number of steps,
+    with their derivatives as the tangent."""
+
+    def __init__(self, theta):
+        self.theta = theta
+        self.seeded = False
+
+    def tangent_begin(self, **seed):
+        assert set(seed) == {"du"}
+        self.seeded = True
+
+    def step(self, tol):
+        return dict(status=0, W=self.theta ** 3, K=np.sin(self.theta))
+
+    def tangent(self):
+        assert self.seeded
+        return dict(dW=3 * self.theta ** 2, dK=np.cos(self.theta))
+
+
+def test_map_eval_forward_mode_is_the_jvp():
+    sim = _AffineMap()
+    j = torch.randn(12, dtype=torch.float64)
+    dj = torch.randn(12, dtype=torch.float64)
+    with fwAD.dual_level():
+        H, dH = fwAD.unpack_dual(pa.map_eval(sim, fwAD.make_dual(j, dj), 1e-12))
+    assert torch.allclose(H, torch.from_numpy(sim.M @ j.numpy() + sim.c), atol=1e-13)
+    assert torch.allclose(dH, torch.from_numpy(sim.M @ dj.numpy()), atol=1e-13)
+    with pytest.raises(NotImplementedError):
+        pa.map_eval(sim, j.clone().requires_grad_(True), 1e-12).sum().backward()
+
+
+def test_energies_after_reverse_and_forward_modes():
+    theta = torch.tensor(0.7, dtype=torch.float64, requires_grad=True)
+    out = pa.energies_after(theta, _Run, lambda th: dict(du=np.zeros(3)), 5, 1e-12)
+    assert torch.allclose(out, torch.tensor([0.7 ** 3, np.sin(0.7)], dtype=torch.float64))
+    (2.0 * out[0] + 3.0 * out[1]).backward()
+    assert abs(theta.grad.item() - (2 * 3 * 0.7 ** 2 + 3 * np.cos(0.7))) < 1e-14
+    with fwAD.dual_level():
+        th = fwAD.make_dual(torch.tensor(0.7, dtype=torch.float64),
+                            torch.tensor(2.0, dtype=torch.float64))
+        _, t = fwAD.unpack_dual(pa.energies_after(th, _Run, lambda x: dict(du=np.zeros(3)), 5,
+                                                  1e-12))
+    assert torch.allclose(t, torch.tensor([2 * 3 * 0.7 ** 2, 2 * np.cos(0.7)],
+                                          dtype=torch.float64))
+    with pytest.raises(ValueError):
+        pa.energies_after(theta, _Run, lambda th: dict(du=np.zeros(3)), 0, 1e-12)
