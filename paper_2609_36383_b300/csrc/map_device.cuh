@@ -896,6 +896,50 @@ constexpr int kTangentSweeps = 0;
 template <>
 constexpr int kTangentSweeps<Dual> = 2;
 
+// The gathers of one inner sweep over the straight orbit that starts at
+// (cell, off) with velocity vb and lasts tsp of the field step: grad phi^{1/2}
+// and D_i A (columns in physical units) averaged along the orbit, and A at
+// its end (A^{n+1}, or A(ta + tsp) for a substep).  False when the orbit
+// crosses more knot planes than the walk handles.
+template <int D, typename T, bool SUB>
+__device__ __forceinline__ bool orbit_gather(const int cell[3], const T off[3], const T dtdx[3],
+                                             T ta, T tsp, const T *__restrict__ nodes,
+                                             const PGeom &pg, const KConst<T> &kc,
+                                             const MapScale<T> &ms, const T vb[3], T gphi[3],
+                                             T Dm[3][3], T Ap[3], int &npieces, int order) {
+  GatherOrbit<D, T, SUB> go;
+  go.nodes = nodes;
+  go.pg = &pg;
+  go.kc = &kc;
+  go.pieces = 0;
+  go.ta = ta;
+  go.tsp = tsp;
+  go.order = order;
+#pragma unroll
+  for (int l = 0; l < 3; l++) {
+    go.cell[l] = cell[l];
+    go.off[l] = off[l];
+    go.del[l] = vb[l] * dtdx[l];
+    go.gphi[l] = T(0);
+    go.Dm[l][0] = go.Dm[l][1] = go.Dm[l][2] = T(0);
+  }
+  const bool ok = walk_orbit<D, T>(go.off, go.del, go, order);
+  npieces += go.pieces;
+  if (!ok) return false;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    gphi[c] = go.gphi[c];
+#pragma unroll
+    for (int j = 0; j < 3; j++) Dm[c][j] = j < D ? go.Dm[c][j] * ms.inv_dx[j] : go.Dm[c][j];
+  }
+  T u1[3];
+#pragma unroll
+  for (int l = 0; l < 3; l++) u1[l] = go.off[l] + go.del[l];
+  if (SUB) interp_At<D, T>(pg, cell, u1, nodes, ta + tsp, Ap, order);
+  else interp_A1<D, T>(pg, cell, u1, nodes, Ap, order);
+  return true;
+}
+
 // One particle's inner Picard iteration (Sec. 4.5, reading R6) over the
 // straight orbit that starts at (cell, off) and lasts tsp of the field step
 // (tsp = 1 unless SUB: then the orbit is the substep [ta, ta + tsp] of a
@@ -914,39 +958,14 @@ __device__ __forceinline__ bool picard(const PushConst<T> &pc, const int cell[3]
   int it, extra = -1;  // sweeps left after the value converged (dual numbers)
 #pragma unroll 1
   for (it = 1; it <= kc.inner_max + kTangentSweeps<T>; it++) {
-    GatherOrbit<D, T, SUB> go;
-    go.nodes = nodes;
-    go.pg = &pg;
-    go.kc = &kc;
-    go.pieces = 0;
-    go.ta = ta;
-    go.tsp = tsp;
-    go.order = order;
-#pragma unroll
-    for (int l = 0; l < 3; l++) {
-      go.cell[l] = cell[l];
-      go.off[l] = off[l];
-      go.del[l] = vb[l] * dtdx[l];
-      go.gphi[l] = T(0);
-      go.Dm[l][0] = go.Dm[l][1] = go.Dm[l][2] = T(0);
-    }
-    const bool ok = walk_orbit<D, T>(go.off, go.del, go, order);
-    npieces += go.pieces;
-    if (!ok) {
+    T gphi[3], Dm[3][3], Ap[3];
+    if (!orbit_gather<D, T, SUB>(cell, off, dtdx, ta, tsp, nodes, pg, kc, ms, vb, gphi, Dm, Ap,
+                                 npieces, order)) {
       sl |= PIC_ST_PIECES;
       break;
     }
-#pragma unroll
-    for (int c = 0; c < 3; c++)
-#pragma unroll
-      for (int j = 0; j < D; j++) go.Dm[c][j] *= ms.inv_dx[j];
-    T u1[3], Ap[3];
-#pragma unroll
-    for (int l = 0; l < 3; l++) u1[l] = go.off[l] + go.del[l];
-    if (SUB) interp_At<D, T>(pg, cell, u1, nodes, ta + tsp, Ap, order);
-    else interp_A1<D, T>(pg, cell, u1, nodes, Ap, order);
     T vn[3], Pc[3];
-    gmhc_push<D, T>(pc, Ap, go.gphi, go.Dm, vb, vn, Pc);
+    gmhc_push<D, T>(pc, Ap, gphi, Dm, vb, vn, Pc);
     T diff = T(0), nrm = T(0), v2 = T(0);
     bool fin = true;
 #pragma unroll
