@@ -176,6 +176,22 @@ int pic_eval_map(pic_ctx *ctx, const double *j, double tol, double *H,
 int pic_eval_map_jvp(pic_ctx *ctx, const double *j, const double *dj, double tol,
                      double *H, double *dH, int on_device);
 
+/* The adjoint of one map evaluation (a vector-Jacobian product): H = H(j)
+   as pic_eval_map computes it and jbar = H'(j)^T ybar.  Transposed from the
+   output back: the Nyquist projector (symmetric); the orbit deposit, whose
+   transpose is the orbit gather of the cotangent current; each particle's
+   inner fixed point vbar = Phi(vbar, F) by implicit differentiation (a
+   3 x 3 solve with (I - Phi_vbar)^T); the gather, whose transpose scatters
+   the push's transpose-vector product with the gather's orbit weights; and
+   the CN field step, mode by mode.  The paper differentiates nothing; the
+   dot product <ybar, H'(j) dj> of pic_eval_map_jvp equals <jbar, dj>.
+   j, ybar, H, jbar: 3*Ng; H or jbar may be NULL.  FP64 contexts with
+   quadratic shapes, no refinement and the cold inner start only (PIC_EARG
+   otherwise).  Allocates its scratch (about 15 * 8 bytes per particle and
+   12 * 8 + 12 * 16 bytes per mesh node) for the call and frees it. */
+int pic_eval_map_vjp(pic_ctx *ctx, const double *j, const double *ybar, double tol,
+                     double *H, double *jbar, int on_device);
+
 /* Forward sensitivity of the whole step (the tangent of the state with
    respect to one parameter of the initial condition), for gradients of
    quantities after many steps.  pic_tangent_begin seeds it at the started

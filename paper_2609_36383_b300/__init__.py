@@ -25,7 +25,7 @@ PIC_FP64, PIC_MIXED = 0, 1
 
 # every symbol include/pic.h declares (checked by the CPU test suite)
 EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
-           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp",
+           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_eval_map_vjp",
            "pic_tangent_begin", "pic_tangent_end", "pic_get_tangent", "pic_num_particles", "pic_get_particles",
            "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
            "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free",
@@ -97,6 +97,7 @@ def lib():
         L.pic_step.argtypes = [_VP, C.c_double, C.POINTER(Report)]
         L.pic_eval_map.argtypes = [_VP, _VP, C.c_double, _VP, _VP, _VP, _VP, C.c_int]
         L.pic_eval_map_jvp.argtypes = [_VP, _VP, _VP, C.c_double, _VP, _VP, C.c_int]
+        L.pic_eval_map_vjp.argtypes = [_VP, _VP, _VP, C.c_double, _VP, _VP, C.c_int]
         L.pic_tangent_begin.argtypes = [_VP, _VP, _VP, _VP, C.c_int]
         L.pic_tangent_end.argtypes = [_VP]
         L.pic_get_tangent.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int]
@@ -258,6 +259,17 @@ class Simulation:
                                     _ptr(dH, 0), 0)
         self._check(rc, allow=(PIC_EINNER,))
         return rc, H, dH
+
+    def eval_map_vjp(self, j, ybar, tol):
+        """H(j) and the adjoint product H'(j)^T ybar (host arrays)."""
+        j = np.ascontiguousarray(j, np.float64)
+        ybar = np.ascontiguousarray(ybar, np.float64)
+        H = np.zeros(3 * self.Ng)
+        jbar = np.zeros(3 * self.Ng)
+        rc = lib().pic_eval_map_vjp(self._h, _ptr(j, 0), _ptr(ybar, 0), float(tol), _ptr(H, 0),
+                                    _ptr(jbar, 0), 0)
+        self._check(rc, allow=(PIC_EINNER,))
+        return rc, H, jbar
 
     def tangent_begin(self, du=None, dA=None, dU=None):
         """Seed the forward sensitivity at the started state: du (3, N) in load

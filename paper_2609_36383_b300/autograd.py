@@ -1,9 +1,9 @@
-"""torch.autograd wrappers of the library's forward-mode derivatives.
+"""torch.autograd wrappers of the library's derivatives.
 
 * ``map_eval(sim, j, tol)``: H(j) = P J_orb(j) of Sec. 4.5 as a function of
   the trial current; its forward-mode derivative (``torch.autograd.forward_ad``
-  dual tensors) is ``pic_eval_map_jvp``.  The reverse mode
-  (an adjoint of the map) is not provided and raises.
+  dual tensors) is ``pic_eval_map_jvp``, its reverse mode (``backward``)
+  ``pic_eval_map_vjp``.
 * ``energies_after(theta, make, seed, steps, tol)``: (W, K) after ``steps``
   implicit steps of the started simulation ``make(theta)`` as a function of
   one scalar parameter theta of the initial condition; ``seed(theta)`` gives
@@ -44,8 +44,11 @@ class _MapEval(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gH):
-        raise NotImplementedError("the adjoint of the map evaluation is not provided; "
-                                  "use forward mode (torch.autograd.forward_ad)")
+        rc, _, jbar = ctx.sim.eval_map_vjp(ctx.j, gH.detach().cpu().numpy().astype(np.float64),
+                                           ctx.tol)
+        if rc:
+            raise RuntimeError(f"map evaluation failed with status {rc}")
+        return torch.from_numpy(jbar).to(gH.device), None, None
 
 
 def map_eval(sim, j: torch.Tensor, tol: float) -> torch.Tensor:

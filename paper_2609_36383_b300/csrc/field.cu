@@ -270,6 +270,36 @@ __global__ void k_energy_tangent_parts(const double2 *phi, const double2 *A, con
   block_sum_write<1>(v, out);
 }
 
+// Transpose of the field step's dependence on the trial current, mode by
+// mode.  k_cn_update maps the transform j^ of the current to the gather
+// spectra i k_c phi^{1/2} (c < dim) and A^{n+1}_c by a real symmetric matrix
+// per mode: d(i k_c phi^{1/2}) = mu k_c (k . dj^) with
+// mu = a dt^2 kappa^2 sigma1 / (4 (1 + a b)), and dA^{n+1}_c = g dj^_c with
+// g = a dt kappa^2 sigma2 / (1 + a b) (a = dt/2, b = dt kappa^2 |k|^2 / 2;
+// continuity enters through rho^{1/2}).  So the adjoint is the same matrix;
+// `scale` folds in the 1/Ng of the inverse transform behind the records.
+__global__ void k_cn_adjoint(const double2 *__restrict__ sbar, double2 *__restrict__ jbar,
+                             SpecGeom sg, double dt, double kap2, double sigma1, double sigma2,
+                             double scale) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= sg.Ng) return;
+  const int Ng = sg.Ng, d = sg.dim;
+  double k[3];
+  const bool nyq = mode_symbols(sg, g, k);
+  if (nyq && sg.project) {
+    for (int c = 0; c < 3; c++) jbar[c * Ng + g] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+  const double a = 0.5 * dt, b = 0.5 * dt * kap2 * k2, inv = 1.0 / (1.0 + a * b);
+  const double mu = a * inv * dt * dt * kap2 * sigma1 * 0.25, gam = a * inv * dt * kap2 * sigma2;
+  double2 ks = make_double2(0.0, 0.0);  // sum_c k_c sbar_phi,c
+  for (int c = 0; c < d; c++) ks = cadd(ks, cscale(k[c], sbar[(size_t)c * Ng + g]));
+  for (int e = 0; e < 3; e++)
+    jbar[e * Ng + g] =
+        cscale(scale, cadd(cscale(mu * k[e], ks), cscale(gam, sbar[(size_t)(d + e) * Ng + g])));
+}
+
 __global__ void k_constraint_parts(const double2 *phi, const double2 *psi, const double2 *rho,
                                    const double2 *A, const double2 *U, SpecGeom sg,
                                    double sigma1, double inv_kap2, double *out) {
@@ -491,6 +521,14 @@ int field_energy_tangent(pic_ctx *ctx, const SpecState &f, const SpecState &df, 
   int e = finish_sum<1>(ctx, nb, &s);
   if (e) return e;
   *dW = s * ctx->g.dV / ctx->g.Ng;
+  return PIC_OK;
+}
+
+int field_cn_adjoint(pic_ctx *ctx, const double2 *sbar, double2 *jbar, double scale) {
+  k_cn_adjoint<<<blocks(ctx->g.Ng), kThreads, 0, ctx->st>>>(
+      sbar, jbar, spec_geom(ctx), ctx->dt, ctx->opt.kappa * ctx->opt.kappa, ctx->opt.sigma1,
+      ctx->opt.sigma2, scale);
+  KCHECK();
   return PIC_OK;
 }
 

@@ -226,6 +226,10 @@ int field_pack_nodes_into(pic_ctx *ctx, double2 *spec, const double *A_n, double
                           double *nodes);
 // phi from Gauss's law and psi from the Lorenz gauge of the state st
 int field_initial_constraints_into(pic_ctx *ctx, const SpecState &st);
+// transpose of the gather spectra's dependence on the trial current:
+// jbar^ (3 Ng modes) from the cotangents sbar^ of [i k phi^{1/2} (dim),
+// A^{n+1} (3)], times scale
+int field_cn_adjoint(pic_ctx *ctx, const double2 *sbar, double2 *jbar, double scale);
 // tangent of the field energy: dW = sum d W / d(phi, A, U) . (dphi, dA, dU)
 int field_energy_tangent(pic_ctx *ctx, const SpecState &st, const SpecState &dst, double *dW);
 int field_energy(pic_ctx *ctx, const double2 *phi_h, const double2 *A_h,

@@ -24,6 +24,9 @@ class _AffineMap:
     def eval_map_jvp(self, j, dj, tol):
         return 0, self.M @ j + self.c, self.M @ dj
 
+    def eval_map_vjp(self, j, ybar, tol):
+        return 0, self.M @ j + self.c, self.M.T @ ybar
+
 
 class _Run:
     """W(theta) = theta^3, K(theta) = sin(theta) after any number of steps,
@@ -45,7 +48,7 @@ class _Run:
         return dict(dW=3 * self.theta ** 2, dK=np.cos(self.theta))
 
 
-def test_map_eval_forward_mode_is_the_jvp():
+def test_map_eval_forward_mode_is_the_jvp_and_reverse_mode_the_vjp():
     sim = _AffineMap()
     j = torch.randn(12, dtype=torch.float64)
     dj = torch.randn(12, dtype=torch.float64)
@@ -53,8 +56,10 @@ def test_map_eval_forward_mode_is_the_jvp():
         H, dH = fwAD.unpack_dual(pa.map_eval(sim, fwAD.make_dual(j, dj), 1e-12))
     assert torch.allclose(H, torch.from_numpy(sim.M @ j.numpy() + sim.c), atol=1e-13)
     assert torch.allclose(dH, torch.from_numpy(sim.M @ dj.numpy()), atol=1e-13)
-    with pytest.raises(NotImplementedError):
-        pa.map_eval(sim, j.clone().requires_grad_(True), 1e-12).sum().backward()
+    jr = j.clone().requires_grad_(True)
+    w = torch.randn(12, dtype=torch.float64)
+    (w * pa.map_eval(sim, jr, 1e-12)).sum().backward()
+    assert torch.allclose(jr.grad, torch.from_numpy(sim.M.T @ w.numpy()), atol=1e-13)
 
 
 def test_energies_after_reverse_and_forward_modes():

@@ -1,10 +1,15 @@
-"""The tangent of one map evaluation (pic_eval_map_jvp) on the CUDA path.
+"""The tangent of one map evaluation (pic_eval_map_jvp) and its adjoint
+(pic_eval_map_vjp) on the CUDA path.
 
 dH = H'(j) dj is checked against central finite differences of the map
 itself (on the GPU and in the FP64 oracle), for linearity, and by using it:
 a Newton-Krylov solve (GMRES(20) with the JVP) of the outer fixed point
 j = H(j) of one step must reach the step's fixed point, which the paper's
 Picard/Anderson iteration (pic_step) also reaches.
+
+The adjoint is checked by the dot-product identity <ybar, H'(j) dj> =
+<H'(j)^T ybar, dj> against the JVP, and against central differences of the
+scalar <ybar, H(j)>.
 
 Tolerances: the map is evaluated with the inner tolerance 1e-14; central
 differences with step h carry a truncation error O(h^2 H''') and a rounding
@@ -80,6 +85,38 @@ def test_jvp_matches_central_differences(name):
     # the value is the map's value
     _, H0, _, _, _ = s.eval_map(j, 1e-14)
     assert np.abs(H - H0).max() < 1e-12 * np.abs(H0).max()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_vjp_is_the_transpose_of_the_jvp(name):
+    """<ybar, H'(j) dj> = <H'(j)^T ybar, dj> for random ybar and dj; both
+    products are exact derivatives of the converged inner fixed point up to
+    the inner tolerance 1e-14, so they agree to about 1e-12 of the gross
+    magnitudes of the two sums."""
+    cfg = CASES[name]()
+    o = make_oracle(cfg)
+    o.start()
+    s = make_gpu(cfg)
+    s.start()
+    gross = gross_scales(cfg)["J"]
+    j, dj = _trial(o, gross)
+    ybar = np.random.default_rng(5).standard_normal(j.shape[0])
+    st, H1, dH = s.eval_map_jvp(j, dj, 1e-14)
+    assert st == 0
+    st, H2, jbar = s.eval_map_vjp(j, ybar, 1e-14)
+    assert st == 0
+    assert np.abs(H1 - H2).max() <= 1e-12 * np.abs(H1).max()
+    lhs, rhs = ybar @ dH, jbar @ dj
+    gross_sum = max(np.abs(ybar * dH).sum(), np.abs(jbar * dj).sum())
+    print(f"{name}: <ybar, J dj> = {lhs:.12e}, <J^T ybar, dj> = {rhs:.12e}, "
+          f"difference {abs(lhs - rhs) / gross_sum:.2e} of the gross sum")
+    assert abs(lhs - rhs) <= 1e-10 * gross_sum
+    # the scalar <ybar, H(j)> by central differences along dj
+    h = 1e-4 * max(np.abs(j).max(), gross) / np.abs(dj).max()
+    _, Hp, _, _, _ = s.eval_map(j + h * dj, 1e-14)
+    _, Hm, _, _, _ = s.eval_map(j - h * dj, 1e-14)
+    fd = ybar @ (Hp - Hm) / (2 * h)
+    assert abs(fd - rhs) <= 2e-6 * gross_sum
 
 
 def test_jvp_is_linear_in_the_direction():

@@ -171,8 +171,8 @@ def test_tangent_end_and_restart_release_it():
 
 
 def test_autograd_wrappers_use_the_library_derivatives(tangent_run):
-    """torch.autograd: reverse mode of energies_after and forward mode of
-    map_eval reproduce the library's tangent and JVP."""
+    """torch.autograd: reverse mode of energies_after and both modes of
+    map_eval reproduce the library's tangent, JVP and VJP."""
     import torch
     import torch.autograd.forward_ad as fwAD
     from paper_2609_36383_b300 import autograd as pa
@@ -200,5 +200,10 @@ def test_autograd_wrappers_use_the_library_derivatives(tangent_run):
     assert st == 0
     assert np.abs(H.numpy() - H_ref).max() <= 1e-12 * np.abs(H_ref).max()
     assert np.abs(dH.numpy() - dH_ref).max() <= 1e-12 * np.abs(dH_ref).max()
-    with pytest.raises(NotImplementedError):
-        pa.map_eval(s, j.clone().requires_grad_(True), 1e-14).sum().backward()
+    # reverse mode through one map evaluation
+    jr = j.clone().requires_grad_(True)
+    yb = torch.from_numpy(np.random.default_rng(2).standard_normal(j.shape[0]))
+    (yb * pa.map_eval(s, jr, 1e-14)).sum().backward()
+    st, _, jbar_ref = s.eval_map_vjp(j.numpy(), yb.numpy(), 1e-14)
+    assert st == 0
+    assert np.abs(jr.grad.numpy() - jbar_ref).max() <= 1e-12 * np.abs(jbar_ref).max()
