@@ -192,6 +192,22 @@ int pic_eval_map_jvp(pic_ctx *ctx, const double *j, const double *dj, double tol
 int pic_eval_map_vjp(pic_ctx *ctx, const double *j, const double *ybar, double tol,
                      double *H, double *jbar, int on_device);
 
+/* Autotuner of the counting-sort interval (sort_every): from the current
+   accepted state, each of the ncand candidate intervals (>= 0; 0 = never
+   sort) runs `steps` implicit steps at tolerance tol, timed with CUDA events
+   on the context's stream; the state is then restored (particles in load
+   order, sorted once if the chosen interval is positive, as pic_start sorts
+   them), sort_every is set to the fastest candidate and returned in *best.
+   ms_per_step (ncand entries, may be NULL) receives each candidate's time.
+   The statistics of pic_get_stats exclude the tuning steps.  The checkpoint
+   passes through host memory (pic_get_particles / pic_get_potentials /
+   pic_set_state), so a forward sensitivity (pic_tangent_begin) is dropped.
+   The paper has no autotuner; the interval trades the sort's cost against
+   the gathers' locality.  A failing step returns its code with the state
+   restored and sort_every unchanged. */
+int pic_tune_sort(pic_ctx *ctx, double tol, int steps, const int *candidates, int ncand,
+                  int *best, double *ms_per_step);
+
 /* Forward sensitivity of the whole step (the tangent of the state with
    respect to one parameter of the initial condition), for gradients of
    quantities after many steps.  pic_tangent_begin seeds it at the started

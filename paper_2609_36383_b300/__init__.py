@@ -25,7 +25,7 @@ PIC_FP64, PIC_MIXED = 0, 1
 
 # every symbol include/pic.h declares (checked by the CPU test suite)
 EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
-           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_eval_map_vjp",
+           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_eval_map_vjp", "pic_tune_sort",
            "pic_tangent_begin", "pic_tangent_end", "pic_get_tangent", "pic_num_particles", "pic_get_particles",
            "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
            "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free",
@@ -98,6 +98,8 @@ def lib():
         L.pic_eval_map.argtypes = [_VP, _VP, C.c_double, _VP, _VP, _VP, _VP, C.c_int]
         L.pic_eval_map_jvp.argtypes = [_VP, _VP, _VP, C.c_double, _VP, _VP, C.c_int]
         L.pic_eval_map_vjp.argtypes = [_VP, _VP, _VP, C.c_double, _VP, _VP, C.c_int]
+        L.pic_tune_sort.argtypes = [_VP, C.c_double, C.c_int, _VP, C.c_int, C.POINTER(C.c_int),
+                                    _VP]
         L.pic_tangent_begin.argtypes = [_VP, _VP, _VP, _VP, C.c_int]
         L.pic_tangent_end.argtypes = [_VP]
         L.pic_get_tangent.argtypes = [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int]
@@ -270,6 +272,17 @@ class Simulation:
                                     _ptr(jbar, 0), 0)
         self._check(rc, allow=(PIC_EINNER,))
         return rc, H, jbar
+
+    def tune_sort(self, tol, steps, candidates=(0, 1, 2, 5, 10, 20)):
+        """Measure each candidate sort interval over `steps` steps from the
+        current state, restore the state and keep the fastest; returns
+        (best interval, ms per step of every candidate)."""
+        cand = np.ascontiguousarray(candidates, np.int32)
+        ms = np.zeros(cand.shape[0])
+        best = C.c_int(-1)
+        self._check(lib().pic_tune_sort(self._h, float(tol), int(steps), _ptr(cand, 0),
+                                        int(cand.shape[0]), C.byref(best), _ptr(ms, 0)))
+        return best.value, ms
 
     def tangent_begin(self, du=None, dA=None, dU=None):
         """Seed the forward sensitivity at the started state: du (3, N) in load
