@@ -180,3 +180,61 @@ def test_tsi_shape_degree_comparison():
         s.close()
     assert out[2][1] == 0  # quadratic shapes never need refinement
     assert out[2][2] < 1e-10 and out[1][2] < 1e-10
+
+
+@pytest.mark.skipif(os.environ.get("PIC_LONG_RUNS") != "1",
+                    reason="600- and 200-step 3D runs (about 3 minutes); set PIC_LONG_RUNS=1")
+@pytest.mark.parametrize("dt,key", [(0.1, "tsi01"), (0.3, "tsi03")])
+def test_tsi_full_run_matches_printed_diagnostics(dt, key):
+    """Sec. 5.1 and Sec. 5.3: TSI-0.1 and TSI-0.3 to T = 60, against what the
+    paper prints for these runs: the first large maximum of |E_x(k_x)| / N_g
+    (0.25296 and 0.25141 near t = 42.6), the amplitude at T = 60 (0.0405932,
+    0.0400176), the |q|-weighted longitudinal RMS velocity at T = 60
+    (0.836845, 0.836425), each within two units of its last printed digit,
+    and the energy error (printed <= 3.53e-12, 6.17e-12).  The mean (max)
+    outer iterations per step are reported beside the printed 6.360 (11) and
+    7.555 (10) and not bounded: they depend on solver details the paper does
+    not pin down, while the fixed points, and with them every diagnostic
+    above, do not."""
+    from oracle import closed_form as cf
+    printed = {"tsi01": dict(tmax=42.6, amax=0.25296, a60=0.0405932, vpar=0.836845,
+                             outer=6.360, outer_max=11),
+               "tsi03": dict(tmax=42.6, amax=0.25141, a60=0.0400176, vpar=0.836425,
+                             outer=7.555, outer_max=10)}[key]
+    G = cf.two_stream_rate(0.25, 0.9, math.pi / 4)
+    cfg = pic_inputs.two_stream_3d(eigen_rate=G, eigen_chi=cf.chi(0.25, math.pi / 4), dt=dt)
+    s = make_gpu(cfg)
+    s.start()
+    n, L = 32, 8 * math.pi
+
+    def mode():
+        f = s.fields()
+        phi = f["phi"].reshape(n, n, n)
+        Ex = -_spectral_deriv(phi, 2, L) - f["U"][: n ** 3].reshape(n, n, n)
+        return abs(np.fft.fftn(Ex)[0, 0, 1]) / n ** 3
+
+    nsteps = int(math.floor(60.0 / dt + 1e-9))
+    ts, amps, outer, dE = [0.0], [mode()], [], 0.0
+    for st in range(1, nsteps + 1):
+        r = s.step(cfg["tol"])
+        assert r["status"] == 0
+        dE = max(dE, abs(r["rel_dE"]))
+        outer.append(r["outer_iters"])
+        ts.append(st * dt)
+        amps.append(mode())
+    amps = np.array(amps)
+    i_max = int(np.argmax(amps))
+    u = s.velocities()
+    v = u / np.sqrt(1.0 + np.sum(u * u, axis=0))
+    wq = np.abs(cfg["w"])
+    vpar = math.sqrt(np.sum(wq * v[0] ** 2) / np.sum(wq))
+    print(f"{key} T=60: first maximum {amps[i_max]:.5f} at t={ts[i_max]:.1f} "
+          f"(paper {printed['amax']} near {printed['tmax']}), amplitude at T=60 {amps[-1]:.7f} "
+          f"(paper {printed['a60']}), v_par,rms {vpar:.6f} (paper {printed['vpar']}), "
+          f"outer iterations mean {np.mean(outer):.3f} max {max(outer)} "
+          f"(paper {printed['outer']} ({printed['outer_max']})), max |dE/E| {dE:.2e}")
+    assert abs(ts[i_max] - printed["tmax"]) <= 0.5 * dt
+    assert abs(amps[i_max] - printed["amax"]) <= 2e-5
+    assert abs(amps[-1] - printed["a60"]) <= 2e-7
+    assert abs(vpar - printed["vpar"]) <= 2e-6
+    assert dE < 1e-11
