@@ -238,3 +238,43 @@ def test_tsi_full_run_matches_printed_diagnostics(dt, key):
     assert abs(amps[-1] - printed["a60"]) <= 2e-7
     assert abs(vpar - printed["vpar"]) <= 2e-6
     assert dE < 1e-11
+
+
+@pytest.mark.skipif(os.environ.get("PIC_LONG_RUNS") != "1",
+                    reason="2500- and 500-step 3D runs (WBI-0.04 alone about 30 minutes); "
+                           "set PIC_LONG_RUNS=1")
+@pytest.mark.parametrize("dt,key", [(0.04, "wbi004"), (0.2, "wbi02")])
+def test_wbi_full_run_residuals(dt, key):
+    """Sec. 5.2: WBI-0.04 and WBI-0.2 to T = 100.  The paper prints the
+    maxima over the run of the Gauss RMS residual (1.22e-12, 5.12e-13), the
+    Lorenz RMS residual (1.40e-13, 3.95e-14), |dE/E| (3.74e-14, 4.13e-13),
+    the chain-rule RMS residual R_A (6.68e-16, 5.57e-16) and the work
+    residual (1.44e-14, 1.31e-13).  The loading of the 25 pairs per cell is
+    not stated in full, so the runs are not identical; each maximum must stay
+    within ten times the printed one (the theorems behind them hold at the
+    solver tolerance for any loading)."""
+    from oracle import closed_form as cf
+    printed = {"wbi004": dict(gauss=1.22e-12, lorenz=1.40e-13, dE=3.74e-14, chain=6.68e-16,
+                              work=1.44e-14),
+               "wbi02": dict(gauss=5.12e-13, lorenz=3.95e-14, dE=4.13e-13, chain=5.57e-16,
+                             work=1.31e-13)}[key]
+    G = cf.weibel_rate(1.0, 0.9, math.pi / 16)
+    cfg = pic_inputs.weibel_3d(eigen_rate=G, eigen_chi=cf.chi(1.0, math.pi / 16), dt=dt)
+    s = make_gpu(cfg, inner_tol_scale=0.1)  # Table 1: WBI inner tolerances 10x tighter
+    s.start()
+    mx = dict(gauss=0.0, lorenz=0.0, dE=0.0, chain=0.0, work=0.0)
+    outer = []
+    for _ in range(int(math.floor(100.0 / dt + 1e-9))):
+        r = s.step(cfg["tol"])
+        assert r["status"] == 0
+        mx["gauss"] = max(mx["gauss"], r["gauss_rms"])
+        mx["lorenz"] = max(mx["lorenz"], r["lorenz_rms"])
+        mx["dE"] = max(mx["dE"], abs(r["rel_dE"]))
+        mx["chain"] = max(mx["chain"], r["chain_rms"])
+        mx["work"] = max(mx["work"], abs(r["work_residual"]))
+        outer.append(r["outer_iters"])
+    print(f"{key} T=100: " + ", ".join(f"max {k} {v:.2e} (paper {printed[k]:.2e})"
+                                       for k, v in mx.items())
+          + f"; outer iterations mean {np.mean(outer):.3f} max {max(outer)}")
+    for k, v in mx.items():
+        assert v <= 10 * printed[k], k
