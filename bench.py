@@ -574,18 +574,49 @@ def oracle_sample(seconds_budget=20.0, steps=1):
                        f"({npart} particles), {n} oracle step(s)")
 
 
-def cpu_baseline_subprocess(args):
+def oracle_one_map_evaluation():
+    """Time one FP64 oracle map evaluation on the 65,536-particle sample (the
+    metric's unit: pushes per map evaluation), for the single-core figure."""
+    import oracle
+    oracle.build()
+    cfg = workload_cfg(seed=0, ppc_beam=2)
+    o = oracle.Oracle(cfg["dim"], cfg["n"], cfg["L"], cfg["x0"], cfg["species"], dt=cfg["dt"],
+                      rho_bg=cfg["rho_bg"])
+    o.set_particles(cfg["x"], cfg["u"], cfg["w"], cfg["sp"])
+    o.set_potentials(cfg["A"], cfg["U"])
+    o.start()
+    npart = cfg["w"].shape[0]
+    j = o.fields()["J"]
+    t0 = time.perf_counter()
+    o.eval_map(j, cfg["tol"])
+    secs = time.perf_counter() - t0
+    return dict(value=npart / secs, unit=UNIT, cores=int(os.environ.get("OMP_NUM_THREADS", 1)),
+                seconds=secs,
+                sample=f"one map evaluation of the {WORKLOAD} mesh with 2 particles/cell/beam "
+                       f"({npart} particles)")
+
+
+def _oracle_subprocess(flag, threads):
     env = dict(os.environ)
-    env.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+    env["OMP_NUM_THREADS"] = str(threads)
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
         env.pop(k, None)
     try:
-        res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"],
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), flag],
                              capture_output=True, text=True, env=env, timeout=600)
         return json.loads(res.stdout.strip().splitlines()[-1])
     except Exception as e:  # report, never fake
         return {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                 "sample": f"failed: {e}"}
+
+
+def cpu_baseline_subprocess(args):
+    """The oracle on all host cores (a bounded sample of steps), and on one
+    core (one map evaluation of the same sample)."""
+    out = _oracle_subprocess("--cpu-sample", int(os.environ.get("OMP_NUM_THREADS",
+                                                                os.cpu_count())))
+    out["one_core"] = _oracle_subprocess("--cpu-sample-one", 1)
+    return out
 
 
 def run_reference(args):
@@ -628,9 +659,13 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 67M-particle case")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling run without the e2e arm")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-sample-one", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_sample:
         print(json.dumps(oracle_sample()), flush=True)
+        return
+    if args.cpu_sample_one:
+        print(json.dumps(oracle_one_map_evaluation()), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
