@@ -479,6 +479,9 @@ def run_ours(args):
             "l2": "flushed before every timed step (256 MiB write)",
             "mean_map_evals_per_step": statistics.mean(r["map_evals"] for r in fp["reports"]),
             "mean_inner_iters": st["inner_iters"] / max(st["pushes"], 1),
+            "mean_outer_iters": statistics.mean(r["outer_iters"] for r in fp["reports"]),
+            # particles x inner iterations per second of the same timed steps
+            "inner_iteration_pushes_per_s": value * st["inner_iters"] / max(st["pushes"], 1),
             "max_abs_rel_dE": fp["rel_dE"],
         },
         "mixed": {
