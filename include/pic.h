@@ -100,6 +100,15 @@ typedef struct {
                                    potential of Eq. A-g-s and depositing its orbit
                                    current weighted by its share of the step; 0..3,
                                    default 0 (off) */
+  int deterministic_deposit;    /* 1: the orbit current is summed without atomics, node by
+                                   node, over nearby particles in an order fixed by their
+                                   cell and position (results identical from run to run,
+                                   and equal across mesh lines that hold equal particle
+                                   configurations); pic_start's point deposits of rho
+                                   and J likewise.  Several times the deposit's cost, a
+                                   checking mode.  FP64 contexts without refinement and
+                                   with at least 8 nodes per active dimension only
+                                   (pic_init returns PIC_EARG otherwise); default 0 */
 } pic_options;
 
 /* Per-step report (Sec. 4.4 diagnostics and solver counters). */

@@ -51,7 +51,7 @@ class Options(C.Structure):
         ("decrease_coef", C.c_double), ("growth_limit", C.c_double), ("tol_abs_ratio", C.c_double),
         ("inner_tol_scale", C.c_double), ("precision", C.c_int), ("mixed_tol_floor", C.c_double),
         ("sort_every", C.c_int), ("cuda_stream", C.c_void_p), ("inner_warm_start", C.c_int),
-        ("order", C.c_int), ("refine_max", C.c_int),
+        ("order", C.c_int), ("refine_max", C.c_int), ("deterministic_deposit", C.c_int),
     ]
 
 

@@ -429,6 +429,10 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
 #undef PIC_MAP_LAUNCH
     KCHECK();
     CK(cudaEventRecordWithFlags(ctx->ev1, ctx->st, evf));
+    if (ctx->opt.deterministic_deposit) {  // replaces the atomic deposit in Jorb
+      int e = det_deposit(ctx, ctx->Jorb, sc_in);
+      if (e) return e;
+    }
     if (final_pass)  // block partials of the work and chain-rule sums
       CK(cudaMemcpyAsync(ctx->psum_host, ctx->psum, sizeof(double) * 2 * nb,
                          cudaMemcpyDeviceToHost, ctx->st));
@@ -649,15 +653,21 @@ int permute_field(pic_ctx *ctx, V *field, int ncomp) {
 int particles_sort(pic_ctx *ctx) {
   if (ctx->np < 2) return PIC_OK;
   const Geom &g = ctx->g;
-  CK(cudaMemsetAsync(ctx->cnt_sort, 0, sizeof(int32_t) * g.Ng, ctx->st));
-  k_sort_keys<<<nblk(ctx->np), kPT, 0, ctx->st>>>(ctx->np, ctx->cap, ctx->cell, g.dim, g.n[0],
-                                                  g.n[0] * g.n[1], ctx->keys, ctx->cnt_sort);
-  KCHECK();
-  k_sort_scan<<<1, 1024, 0, ctx->st>>>(ctx->cnt_sort, g.Ng);
-  KCHECK();
-  k_sort_slots<<<nblk(ctx->np), kPT, 0, ctx->st>>>(ctx->np, ctx->keys, ctx->cnt_sort, ctx->tmp_l);
-  KCHECK();
   int e;
+  if (ctx->opt.deterministic_deposit && ctx->det_count) {
+    // the same cell order, with the order inside a cell fixed
+    if ((e = det_sort_slots(ctx, ctx->tmp_l))) return e;
+  } else {
+    CK(cudaMemsetAsync(ctx->cnt_sort, 0, sizeof(int32_t) * g.Ng, ctx->st));
+    k_sort_keys<<<nblk(ctx->np), kPT, 0, ctx->st>>>(ctx->np, ctx->cap, ctx->cell, g.dim, g.n[0],
+                                                    g.n[0] * g.n[1], ctx->keys, ctx->cnt_sort);
+    KCHECK();
+    k_sort_scan<<<1, 1024, 0, ctx->st>>>(ctx->cnt_sort, g.Ng);
+    KCHECK();
+    k_sort_slots<<<nblk(ctx->np), kPT, 0, ctx->st>>>(ctx->np, ctx->keys, ctx->cnt_sort,
+                                                     ctx->tmp_l);
+    KCHECK();
+  }
   if ((e = permute_field<int32_t>(ctx, ctx->cell, g.dim))) return e;
   if (ctx->rsize == 8) {
     if ((e = permute_field<double>(ctx, (double *)ctx->off, g.dim))) return e;

@@ -55,6 +55,7 @@ int ilog2(int n) { int l = 0; while ((1 << l) < n) l++; return l; }
 
 void free_all(pic_ctx *ctx) {
   tangent_free(ctx);
+  det_free(ctx);
   void *ptrs[] = {ctx->cell, ctx->off, ctx->P, ctx->w, ctx->sp, ctx->id, ctx->Am, ctx->v0,
                   ctx->vbar, ctx->Pnew, ctx->iters, ctx->u_in, ctx->tmp_d, ctx->tmp_i, ctx->psum,
                   ctx->phi_h, ctx->psi_h, ctx->rho_h, ctx->A_h, ctx->U_h, ctx->A_real, ctx->J_acc,
@@ -361,6 +362,7 @@ void pic_default_options(pic_options *o) {
   o->inner_warm_start = 0;
   o->order = 2;
   o->refine_max = 0;
+  o->deterministic_deposit = 0;
 }
 
 int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, int nspecies,
@@ -382,8 +384,13 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, in
       o.anderson_m < 0 || o.anderson_m > PIC_MAX_ANDERSON || o.backtrack_levels < 1 ||
       (o.precision != PIC_FP64 && o.precision != PIC_MIXED) || !(o.kappa > 0.0) ||
       !(o.sigma1 > 0.0) || !(o.sigma2 > 0.0) || (o.order != 1 && o.order != 2) ||
-      o.refine_max < 0 || o.refine_max > 3)
+      o.refine_max < 0 || o.refine_max > 3 ||
+      (o.deterministic_deposit && (o.precision != PIC_FP64 || o.refine_max != 0)))
     return PIC_EARG;
+  // the deterministic deposit's node gather spans at least 5 nodes per dimension
+  if (o.deterministic_deposit)
+    for (int a = 0; a < grid->dim; a++)
+      if (grid->n[a] < 8) return PIC_EARG;
   pic_ctx *ctx = new (std::nothrow) pic_ctx();
   if (!ctx) return PIC_ENOMEM;
   ctx->opt = o;
@@ -526,7 +533,12 @@ int pic_start(pic_ctx *ctx, pic_report *out) {
   std::vector<double> bg(Ng, ctx->opt.rho_bg);
   CK(cudaMemcpyAsync(rho, bg.data(), sizeof(double) * Ng, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemsetAsync(ctx->J_acc, 0, sizeof(double) * 3 * Ng, ctx->st));
-  if ((e = particles_point_deposit(ctx, rho, ctx->J_acc))) return e;
+  if ((e = det_alloc(ctx))) return e;
+  if (ctx->opt.deterministic_deposit) {
+    if ((e = det_point_deposit(ctx, rho, ctx->J_acc, make_sc(ctx, 0.0, 0.0)))) return e;
+  } else if ((e = particles_point_deposit(ctx, rho, ctx->J_acc))) {
+    return e;
+  }
   if ((e = set_fields_real(ctx, rho, ctx->rho_h, 1))) return e;
   if ((e = field_project_h(ctx, ctx->rho_h, 1))) return e;
   if ((e = set_fields_real(ctx, ctx->J_acc, ctx->jh, 3))) return e;
@@ -790,6 +802,7 @@ int pic_set_state(pic_ctx *ctx, int64_t n, const int32_t *species, const double 
   if ((e = particles_refresh_A(ctx))) return e;
   if ((e = copy_in(ctx, ctx->J_acc, J, 3 * Ng, on_device))) return e;
   CK(cudaStreamSynchronize(ctx->st));
+  if ((e = det_alloc(ctx))) return e;
   ctx->E0 = E0;
   ctx->started = 1;
   ctx->pending_mech = 0;

@@ -170,6 +170,11 @@ struct pic_ctx {
   int ngraphs;
   int graphs_off;  // capture failed once: launch directly
   TangentState *tan;  // forward sensitivity, or null
+  // deterministic deposit (option deterministic_deposit): per-cell particle
+  // lists and the deposit's reach
+  int32_t *det_count = nullptr, *det_cursor = nullptr, *det_start = nullptr, *det_list = nullptr;
+  int *det_reach = nullptr;
+  int64_t det_cap = 0;
 };
 
 // Gauss-Legendre nodes t and weights w of an n-point rule on [0, 1]
@@ -261,6 +266,18 @@ int particles_export_eval(pic_ctx *ctx, double *vbar, double *Pnew, int32_t *ite
                           int on_device);
 int particles_export_u(pic_ctx *ctx, double *u, int on_device);
 int particles_sort(pic_ctx *ctx);
+
+// ---------------------------------------------------------------- det.cu
+// buffers of the deterministic deposit (pic_start, pic_set_state); free them
+int det_alloc(pic_ctx *ctx);
+void det_free(pic_ctx *ctx);
+// the orbit current of the last map evaluation, summed node by node in a
+// fixed order from the particles' vbar, into J (overwriting it)
+int det_deposit(pic_ctx *ctx, double *J, const StepConst &sc);
+// pic_start's point deposits of rho (added to its contents) and J, in a fixed order
+int det_point_deposit(pic_ctx *ctx, double *rho, double *J, const StepConst &sc);
+// the particle sort's slots in the deterministic order
+int det_sort_slots(pic_ctx *ctx, int64_t *slot);
 
 // ---------------------------------------------------------------- tangent.cu
 // advance the tangent through the converged step (before the commit) and

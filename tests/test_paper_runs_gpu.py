@@ -278,3 +278,36 @@ def test_wbi_full_run_residuals(dt, key):
           + f"; outer iterations mean {np.mean(outer):.3f} max {max(outer)}")
     for k, v in mx.items():
         assert v <= 10 * printed[k], k
+
+
+@pytest.mark.skipif(os.environ.get("PIC_LONG_RUNS") != "1",
+                    reason="a 600-step 3D run with the deterministic deposit (about 3 minutes); "
+                           "set PIC_LONG_RUNS=1")
+def test_tsi_projected_transverse_velocity_with_deterministic_deposit():
+    """Sec. 5.3: TSI-0.1 to T = 60 with the projector and the deterministic
+    deposit.  The loading is the same in every transverse line, so the
+    transverse modes are seeded only by rounding; the atomic deposit sums
+    each node's contributions in a different order on every line, the
+    deterministic one in the same order.  The transverse RMS velocity is
+    reported beside the paper's 2.29e-12; it is bounded as in the projection
+    study."""
+    from oracle import closed_form as cf
+    G = cf.two_stream_rate(0.25, 0.9, math.pi / 4)
+    cfg = pic_inputs.two_stream_3d(eigen_rate=G, eigen_chi=cf.chi(0.25, math.pi / 4))
+    s = make_gpu(cfg, deterministic_deposit=1)
+    s.start()
+    dE = 0.0
+    for _ in range(600):
+        r = s.step(cfg["tol"])
+        assert r["status"] == 0
+        dE = max(dE, abs(r["rel_dE"]))
+    u = s.velocities()
+    v = u / np.sqrt(1.0 + np.sum(u * u, axis=0))
+    wq = np.abs(cfg["w"])
+    vperp = math.sqrt(np.sum(wq * (v[1] ** 2 + v[2] ** 2)) / np.sum(wq))
+    vpar = math.sqrt(np.sum(wq * v[0] ** 2) / np.sum(wq))
+    print(f"TSI-0.1 T=60, deterministic deposit: v_perp,rms {vperp:.3e} (paper 2.29e-12), "
+          f"v_par,rms {vpar:.6f} (paper 0.836845), max |dE/E| {dE:.2e}")
+    assert vperp < 1e-6
+    assert abs(vpar - 0.836845) <= 2e-6
+    assert dE < 1e-11
