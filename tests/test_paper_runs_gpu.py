@@ -120,9 +120,10 @@ def test_tsi_nyquist_projection_on_off():
     The charge-weighted transverse RMS velocity (Eq. transverse-rms-results)
     stays near roundoff with projection (paper: 2.28724e-12; measured here
     2.78e-8) and grows to order one without it (paper: 0.366930; measured
-    0.519).  The projected value is seeded by rounding noise that differs
-    between transverse lines (the deposit's atomic summation order is not
-    the same on every line), so it is bounded, not matched."""
+    0.519).  The projected value grows from rounding noise that differs
+    between transverse lines; the deposit's summation order is not its
+    source (the deterministic deposit gives the same order of magnitude), so
+    it is bounded, not matched."""
     from oracle import closed_form as cf
     G = cf.two_stream_rate(0.25, 0.9, math.pi / 4)
     out = {}
