@@ -108,7 +108,8 @@ typedef struct {
                                    and J likewise.  Several times the deposit's cost, a
                                    checking mode.  FP64 contexts without refinement and
                                    with at least 8 nodes per active dimension only
-                                   (pic_init returns PIC_EARG otherwise); default 0 */
+                                   (pic_init returns PIC_EARG otherwise), and not in a
+                                   batch (pic_batch_init rejects it); default 0 */
 } pic_options;
 
 /* Per-step report (Sec. 4.4 diagnostics and solver counters). */

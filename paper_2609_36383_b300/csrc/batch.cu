@@ -1504,7 +1504,8 @@ int pic_batch_init(pic_batch **out, int B, const int *n, const double *L, const 
   if (o.anderson_m < 0 || o.anderson_m > kMh || o.backtrack_levels < 1 || o.outer_max < 1 ||
       o.inner_max < 1 || o.gl_points < 0 || o.gl_points > PIC_MAX_GL ||
       (o.precision != PIC_FP64 && o.precision != PIC_MIXED) || !(o.kappa > 0.0) ||
-      (o.order != 1 && o.order != 2) || o.refine_max < 0 || o.refine_max > 3)
+      (o.order != 1 && o.order != 2) || o.refine_max < 0 || o.refine_max > 3 ||
+      o.deterministic_deposit)  // the batch deposits with atomics only
     return PIC_EARG;
   for (int s = 0; s < nspecies; s++)
     if (!(species[s].m > 0.0)) return PIC_EARG;

@@ -76,3 +76,33 @@ def test_batch_init_rejects_bad_sizes_without_touching_the_gpu(libpic):
     n[1] = 2048  # above the largest instance mesh
     assert P.lib().pic_batch_init(ctypes.byref(h), 2, n, L, None, npart, sp, 1, 0.1,
                                   None) == P.PIC_EARG
+
+
+def test_deterministic_deposit_rejected_where_unsupported_without_touching_the_gpu(libpic):
+    """The deterministic deposit needs FP64, no refinement, at least 8 nodes
+    per active dimension, and a single context; pic_init and pic_batch_init
+    refuse it otherwise before any device call."""
+    import paper_2609_36383_b300 as P
+    sp = (P.Species * 1)(P.Species(-1.0, 1.0))
+    g = P.Grid()
+    g.dim = 2
+    for a in range(3):
+        g.n[a] = 16 if a < 2 else 1
+        g.L[a] = 1.0
+    h = ctypes.c_void_p()
+    for field, value in (("precision", P.PIC_MIXED), ("refine_max", 1)):
+        o = P.default_options()
+        o.deterministic_deposit = 1
+        setattr(o, field, value)
+        assert P.lib().pic_init(ctypes.byref(h), ctypes.byref(g), sp, 1, 0.1,
+                                ctypes.byref(o)) == P.PIC_EARG
+    o = P.default_options()
+    o.deterministic_deposit = 1
+    g.n[1] = 4  # too small for the node gather's stencil
+    assert P.lib().pic_init(ctypes.byref(h), ctypes.byref(g), sp, 1, 0.1,
+                            ctypes.byref(o)) == P.PIC_EARG
+    n = (ctypes.c_int * 2)(16, 32)
+    L = (ctypes.c_double * 2)(1.0, 1.0)
+    npart = (ctypes.c_int64 * 2)(10, 10)
+    assert P.lib().pic_batch_init(ctypes.byref(h), 2, n, L, None, npart, sp, 1, 0.1,
+                                  ctypes.byref(o)) == P.PIC_EARG
