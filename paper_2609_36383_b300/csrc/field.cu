@@ -16,6 +16,7 @@
 //    Gauss and Lorenz residuals (Eq. constraint-residuals) and the mesh side
 //    of the work residual (Eq. work-diagnostic).
 #include "pic_internal.cuh"
+#include "csum.cuh"
 
 #include <cmath>
 
@@ -201,18 +202,19 @@ __global__ void k_initial_constraints(double2 *phi, double2 *psi, const double2 
 // ---- block reductions -------------------------------------------------------
 template <int NQ>
 __device__ void block_sum_write(double (&v)[NQ], double *out) {
-  __shared__ double sh[NQ][kThreads / 32];
+  // compensated: each block writes NQ (sum, error) pairs
+  __shared__ CSum sh[NQ][kThreads / 32];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int q = 0; q < NQ; q++) {
-    double x = v[q];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    CSum x = csum_warp(CSum{v[q], 0.0});
     if (lane == 0) sh[q][wid] = x;
   }
   __syncthreads();
   if (threadIdx.x < NQ) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); w++) s += sh[threadIdx.x][w];
-    out[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
+    CSum t = csum_zero();
+    for (int w = 0; w < (int)(blockDim.x / 32); w++) t = csum_merge(t, sh[threadIdx.x][w]);
+    out[((size_t)blockIdx.x * NQ + threadIdx.x) * 2] = t.s;
+    out[((size_t)blockIdx.x * NQ + threadIdx.x) * 2 + 1] = t.c;
   }
 }
 
@@ -398,27 +400,30 @@ __global__ void k_mesh_work_real(const double *H, const double2 *spec, int Ng, i
 
 template <int NQ>
 __global__ void k_sum_partials(const double *parts, int nblk, double *out) {
-  // one block; fixed summation order for run-to-run reproducibility
-  __shared__ double sh[NQ][kThreads];
+  // one block; fixed summation order for run-to-run reproducibility; the
+  // block partials are (sum, error) pairs merged with compensation
+  __shared__ CSum sh[NQ][kThreads];
   for (int q = 0; q < NQ; q++) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += parts[(size_t)b * NQ + q];
-    sh[q][threadIdx.x] = s;
+    CSum t = csum_zero();
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+      t = csum_merge(t, CSum{parts[((size_t)b * NQ + q) * 2], parts[((size_t)b * NQ + q) * 2 + 1]});
+    sh[q][threadIdx.x] = t;
   }
   __syncthreads();
   for (int st = blockDim.x / 2; st > 0; st >>= 1) {
     if ((int)threadIdx.x < st)
-      for (int q = 0; q < NQ; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + st];
+      for (int q = 0; q < NQ; q++) sh[q][threadIdx.x] = csum_merge(sh[q][threadIdx.x], sh[q][threadIdx.x + st]);
     __syncthreads();
   }
-  if (threadIdx.x < NQ) out[threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < NQ) out[threadIdx.x] = csum_value(sh[threadIdx.x][0]);
 }
 
 template <int NQ>
 int finish_sum(pic_ctx *ctx, int nblk, double *host_out) {
-  k_sum_partials<NQ><<<1, kThreads, 0, ctx->st>>>(ctx->red, nblk, ctx->red + (size_t)nblk * NQ);
+  k_sum_partials<NQ><<<1, kThreads, 0, ctx->st>>>(ctx->red, nblk,
+                                                   ctx->red + (size_t)nblk * NQ * 2);
   KCHECK();
-  CK(cudaMemcpyAsync(ctx->red_host, ctx->red + (size_t)nblk * NQ, sizeof(double) * NQ,
+  CK(cudaMemcpyAsync(ctx->red_host, ctx->red + (size_t)nblk * NQ * 2, sizeof(double) * NQ,
                      cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   for (int q = 0; q < NQ; q++) host_out[q] = ctx->red_host[q];

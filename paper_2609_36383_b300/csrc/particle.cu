@@ -2,6 +2,7 @@
 // the particle map (map_device.cuh), loading and export, step start, commit,
 // kinetic energy, point deposits for pic_start, and the counting sort.
 #include "map_device.cuh"
+#include "csum.cuh"
 
 #include <cmath>
 
@@ -137,8 +138,8 @@ __global__ void k_commit(int64_t np, int64_t cap, int32_t *cell, T *off, T *P,
 }
 
 // kinetic energy m kappa^2 (gamma - 1) = |p|^2 / (m (gamma + 1)), p = P - q A_h(x)
-// (Eq. Kkin-nondim): per particle in the particle real type, summed in that
-// type over a warp and in FP64 from there on (block partials summed on the host)
+// (Eq. Kkin-nondim): per particle in the particle real type, summed in FP64
+// with compensation (block (sum, error) pairs merged on the host)
 template <int D, typename T>
 __global__ void __launch_bounds__(kPT)
 k_kinetic(PView<T> pv, const T *__restrict__ AT, PGeom pg, KConst<T> kc, double *psum) {
@@ -164,14 +165,15 @@ k_kinetic(PView<T> pv, const T *__restrict__ AT, PGeom pg, KConst<T> kc, double 
     T gam = sqrt(T(1) + p2 * im * im / (kc.kappa * kc.kappa));
     k = p2 * im / (gam + T(1));
   }
-  for (int o = 16; o > 0; o >>= 1) k += __shfl_down_sync(0xffffffffu, k, o);
-  __shared__ double sh[kPT / 32];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = widen(k);
+  const CSum kw = csum_warp(CSum{widen(k), 0.0});
+  __shared__ CSum sh[kPT / 32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = kw;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kPT / 32; w++) t += sh[w];
-    psum[blockIdx.x] = t;
+    CSum t = csum_zero();
+    for (int w = 0; w < kPT / 32; w++) t = csum_merge(t, sh[w]);
+    psum[2 * blockIdx.x] = t.s;
+    psum[2 * blockIdx.x + 1] = t.c;
   }
 }
 
@@ -449,12 +451,15 @@ int particles_map_finish(pic_ctx *ctx, double *work_sum, double *chain_sum, Eval
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     ctx->map_ms += ms;
     ctx->map_launches++;
-    if (ctx->map_final) {  // fixed summation order: reproducible diagnostics
+    if (ctx->map_final) {  // fixed order, compensated: reproducible diagnostics
       int nb = nblk(ctx->np);
+      CSum cw = csum_zero(), cc = csum_zero();
       for (int b = 0; b < nb; b++) {
-        work += ctx->psum_host[2 * b];
-        chain += ctx->psum_host[2 * b + 1];
+        csum_add(cw, ctx->psum_host[2 * b]);
+        csum_add(cc, ctx->psum_host[2 * b + 1]);
       }
+      work = csum_value(cw);
+      chain = csum_value(cc);
     }
   }
   *cnt = *ctx->cnt_host;
@@ -485,12 +490,13 @@ int particles_kinetic(pic_ctx *ctx, double *K) {
   PIC_DISPATCH(ctx, (k_kinetic<DD, RT><<<nb, kPT, 0, ctx->st>>>(
                          pview<RT>(ctx), A_typed<RT>(ctx), pg, kconst<RT>(sc, pg), ctx->psum)));
   KCHECK();
-  CK(cudaMemcpyAsync(ctx->psum_host, ctx->psum, sizeof(double) * nb, cudaMemcpyDeviceToHost,
-                     ctx->st));
+  CK(cudaMemcpyAsync(ctx->psum_host, ctx->psum, sizeof(double) * 2 * nb,
+                     cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
-  double k = 0.0;
-  for (int b = 0; b < nb; b++) k += ctx->psum_host[b];  // fixed order
-  *K = k;
+  CSum k = csum_zero();
+  for (int b = 0; b < nb; b++)  // fixed order
+    k = csum_merge(k, CSum{ctx->psum_host[2 * b], ctx->psum_host[2 * b + 1]});
+  *K = csum_value(k);
   return PIC_OK;
 }
 

@@ -93,7 +93,9 @@ int alloc_mesh(pic_ctx *ctx) {
   CK(cudaMalloc((void **)&ctx->dR, R * 3 * Ng * M));
   CK(cudaMalloc(&ctx->nodes, (size_t)ctx->rsize * node_record_len((int)d) * Ng));
   CK(cudaMalloc(&ctx->nodes_u, (size_t)ctx->rsize * 4 * Ng));
-  size_t nred = 2 * (Ng / 256 + 2) + 1024 * 48 + 64;
+  // block partials of the reductions: compensated (sum, error) pairs of up
+  // to 3 quantities per block (field.cu), 8 doubles per block (reduce.cu)
+  size_t nred = 8 * (Ng / 256 + 2) + 1024 * 48 + 64;
   CK(cudaMalloc((void **)&ctx->red, R * nred));
   CK(cudaMallocHost((void **)&ctx->red_host, R * 64));
   CK(cudaMalloc((void **)&ctx->cnt_dev, sizeof(EvalCounters)));

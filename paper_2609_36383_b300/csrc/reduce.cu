@@ -9,17 +9,22 @@
 // Block partials are summed by a single block in a fixed order, so results
 // are identical from run to run.
 #include "pic_internal.cuh"
+#include "csum.cuh"
 
 namespace {
 
 constexpr int kT = 256;
 constexpr int kMaxBlocks = 1024;
 
+// r = H - j; per block the compensated sums of |r|^2, |H|^2, |j|^2 as
+// (sum, error) pairs and the largest scaled node residual (8 doubles)
 __global__ void k_resid(const double *__restrict__ H, const double *__restrict__ j,
                         double *__restrict__ r, int Ng, double tau_r, double tau_a,
                         double *parts) {
-  __shared__ double sh[4][kT / 32];
-  double s_r = 0, s_h = 0, s_j = 0, mx = 0;
+  __shared__ CSum sh[3][kT / 32];
+  __shared__ double shm[kT / 32];
+  CSum acc[3] = {csum_zero(), csum_zero(), csum_zero()};
+  double mx = 0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < Ng; g += gridDim.x * blockDim.x) {
     double rr = 0, hh = 0, jj = 0;
 #pragma unroll
@@ -31,47 +36,53 @@ __global__ void k_resid(const double *__restrict__ H, const double *__restrict__
       hh += hv * hv;
       jj += jv * jv;
     }
-    s_r += rr;
-    s_h += hh;
-    s_j += jj;
+    csum_add(acc[0], rr);
+    csum_add(acc[1], hh);
+    csum_add(acc[2], jj);
     mx = fmax(mx, sqrt(rr) / (tau_a + 0.5 * tau_r * (sqrt(hh) + sqrt(jj))));
   }
-  double v[4] = {s_r, s_h, s_j, mx};
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int q = 0; q < 4; q++) {
-    double x = v[q];
-    for (int o = 16; o > 0; o >>= 1) {
-      double y = __shfl_down_sync(0xffffffffu, x, o);
-      x = (q == 3) ? fmax(x, y) : x + y;
-    }
+  for (int q = 0; q < 3; q++) {
+    CSum x = csum_warp(acc[q]);
     if (lane == 0) sh[q][wid] = x;
   }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if (lane == 0) shm[wid] = mx;
   __syncthreads();
-  if (threadIdx.x < 4) {
-    double s = 0;
-    for (int w = 0; w < kT / 32; w++)
-      s = (threadIdx.x == 3) ? fmax(s, sh[threadIdx.x][w]) : s + sh[threadIdx.x][w];
-    parts[blockIdx.x * 4 + threadIdx.x] = s;
+  if (threadIdx.x < 3) {
+    CSum t = csum_zero();
+    for (int w = 0; w < kT / 32; w++) t = csum_merge(t, sh[threadIdx.x][w]);
+    parts[blockIdx.x * 8 + 2 * threadIdx.x] = t.s;
+    parts[blockIdx.x * 8 + 2 * threadIdx.x + 1] = t.c;
+  } else if (threadIdx.x == 3) {
+    double m = 0;
+    for (int w = 0; w < kT / 32; w++) m = fmax(m, shm[w]);
+    parts[blockIdx.x * 8 + 6] = m;
   }
 }
 
 __global__ void k_resid_final(const double *parts, int nb, double *out) {
-  __shared__ double sh[4][kT];
-  for (int q = 0; q < 4; q++) {
-    double s = 0;
+  __shared__ CSum sh[3][kT];
+  __shared__ double shm[kT];
+  for (int q = 0; q < 3; q++) {
+    CSum t = csum_zero();
     for (int b = threadIdx.x; b < nb; b += blockDim.x)
-      s = (q == 3) ? fmax(s, parts[b * 4 + q]) : s + parts[b * 4 + q];
-    sh[q][threadIdx.x] = s;
+      t = csum_merge(t, CSum{parts[b * 8 + 2 * q], parts[b * 8 + 2 * q + 1]});
+    sh[q][threadIdx.x] = t;
   }
+  double m = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fmax(m, parts[b * 8 + 6]);
+  shm[threadIdx.x] = m;
   __syncthreads();
   for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-    if ((int)threadIdx.x < st)
-      for (int q = 0; q < 4; q++)
-        sh[q][threadIdx.x] = (q == 3) ? fmax(sh[q][threadIdx.x], sh[q][threadIdx.x + st])
-                                      : sh[q][threadIdx.x] + sh[q][threadIdx.x + st];
+    if ((int)threadIdx.x < st) {
+      for (int q = 0; q < 3; q++) sh[q][threadIdx.x] = csum_merge(sh[q][threadIdx.x], sh[q][threadIdx.x + st]);
+      shm[threadIdx.x] = fmax(shm[threadIdx.x], shm[threadIdx.x + st]);
+    }
     __syncthreads();
   }
-  if (threadIdx.x < 4) out[threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < 3) out[threadIdx.x] = csum_value(sh[threadIdx.x][0]);
+  else if (threadIdx.x == 3) out[3] = shm[0];
 }
 
 constexpr int kMaxDots = 48;  // M(M+1)/2 + M for the largest history M = 8
@@ -161,9 +172,9 @@ int resid_launch(pic_ctx *ctx, const double *Hv, const double *jv, double *rv, d
   int nb = grid_for(Ng);
   k_resid<<<nb, kT, 0, ctx->st>>>(Hv, jv, rv, Ng, tau_r, tau_a, ctx->red);
   KCHECK();
-  k_resid_final<<<1, kT, 0, ctx->st>>>(ctx->red, nb, ctx->red + (size_t)nb * 4);
+  k_resid_final<<<1, kT, 0, ctx->st>>>(ctx->red, nb, ctx->red + (size_t)nb * 8);
   KCHECK();
-  CK(cudaMemcpyAsync(ctx->red_host, ctx->red + (size_t)nb * 4, sizeof(double) * 4,
+  CK(cudaMemcpyAsync(ctx->red_host, ctx->red + (size_t)nb * 8, sizeof(double) * 4,
                      cudaMemcpyDeviceToHost, ctx->st));
   return PIC_OK;
 }
