@@ -279,6 +279,76 @@ int pic_set_state(pic_ctx *ctx, int64_t n, const int32_t *species, const double 
                   const double *psi, const double *A, const double *U,
                   const double *rho, const double *J, double E0, int on_device);
 
+/* Checkpoint image: the accepted state of a context as bytes, for exact
+   resume (library support; the paper has no counterpart).  Unlike
+   pic_set_state, which takes the real-space arrays of pic_get_* and passes
+   them through an FFT, the image holds the device state itself (particles in
+   storage order as cell index + in-cell offset, potentials as spectral
+   coefficients), so a context that loads it continues with the very bits the
+   saving context had.  With deterministic_deposit = 1 the resumed steps equal
+   the uninterrupted run's bit for bit; with the atomic deposit they agree to
+   the deposit's summation-order rounding.
+
+   Layout, all little-endian: this 256-byte header, then 13 sections, each
+   starting on a 16-byte boundary (zero padding counted in the checksum):
+     cell  int32  [dim][np]    nearest node per active dimension
+     off   real   [dim][np]    offset in node units, in [-1/2, 1/2]
+     P     real   [3][np]      canonical momentum
+     w     f64    [np]         weight
+     sp    int32  [np]         species
+     id    int64  [np]         load-order index (a permutation of 0..np-1)
+     phi, psi, rho  c128 [Ng] each; A, U  c128 [3][Ng]  unnormalised DFT
+                               coefficients of the accepted potentials
+     A     f64    [3][Ng]      A^n in real space
+     J     f64    [3][Ng]      accepted current (seed of the next outer solve)
+   where real is f64 for PIC_FP64 and f32 for PIC_MIXED and c128 is a
+   (re, im) pair of f64. */
+typedef struct {
+  char magic[8];          /* "PICCKPT1" */
+  uint32_t version;       /* 1 */
+  uint32_t header_bytes;  /* 256 */
+  uint64_t total_bytes;   /* header + payload */
+  uint64_t checksum;      /* 64-bit FNV-1a of the bytes after the header */
+  int32_t dim, n[3];      /* mesh; n = 1 in ignorable dimensions */
+  int32_t precision;      /* PIC_FP64 or PIC_MIXED */
+  int32_t nspecies;
+  int32_t sort_every;     /* sort interval in effect (pic_tune_sort may set it) */
+  int32_t reserved0;
+  double L[3], x0[3];
+  double q[4], m[4];      /* species charge and mass per unit weight */
+  double dt;              /* time step of the saving context (not checked on load) */
+  double E0;              /* reference total energy for rel_dE */
+  int64_t np;             /* particles */
+  int64_t steps_done;     /* accepted steps since pic_start (sort schedule) */
+  uint8_t reserved[48];
+} pic_checkpoint_header;
+
+/* Size in bytes of the image of the context's current state. */
+int pic_checkpoint_bytes(const pic_ctx *ctx, uint64_t *bytes);
+
+/* Write the image into a HOST buffer of exactly pic_checkpoint_bytes bytes
+   (PIC_EARG otherwise; PIC_ESTATE before pic_start).  Synchronises the
+   context's stream. */
+int pic_checkpoint_save(pic_ctx *ctx, void *image, uint64_t bytes);
+
+/* Validate an image on the host (no context and no GPU needed): magic,
+   version, sizes, checksum, and every value later used as an index (cells
+   inside the mesh, offsets within [-1/2, 1/2], species below nspecies, the
+   load-order indices a permutation).  Fills *header (may be NULL) and, on
+   PIC_EARG, writes the reason into why (may be NULL, why_len bytes with the
+   terminating zero). */
+int pic_checkpoint_inspect(const void *image, uint64_t bytes, pic_checkpoint_header *header,
+                           char *why, int why_len);
+
+/* Replace the context's state with a validated image.  The context must have
+   the image's mesh (dim, n, L, x0 bitwise), precision and species (q, m);
+   its options (tolerances, deposit mode, ...) stay its own except the sort
+   interval, which the image sets.  Any forward sensitivity is dropped.
+   PIC_EARG (nothing changed) for an invalid or foreign image; after a
+   PIC_ECUDA / PIC_ENOMEM the context refuses pic_step (PIC_ESTATE) until a
+   state is set again. */
+int pic_checkpoint_load(pic_ctx *ctx, const void *image, uint64_t bytes);
+
 /* Counters of the work this context has done (library profiling support;
    the paper has no counterpart).  map_ms is the device time of the particle
    map kernel (inner solves + deposit) measured with CUDA events recorded on

@@ -27,7 +27,9 @@ PIC_FP64, PIC_MIXED = 0, 1
 EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
            "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_eval_map_vjp", "pic_tune_sort",
            "pic_tangent_begin", "pic_tangent_end", "pic_get_tangent", "pic_num_particles", "pic_get_particles",
-           "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_get_stats", "pic_reset_stats",
+           "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_checkpoint_bytes",
+           "pic_checkpoint_save", "pic_checkpoint_inspect", "pic_checkpoint_load",
+           "pic_get_stats", "pic_reset_stats",
            "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free",
            "pic_batch_init", "pic_batch_set_instance", "pic_batch_start", "pic_batch_step",
            "pic_batch_num_particles", "pic_batch_get_particles", "pic_batch_get_potentials",
@@ -53,6 +55,31 @@ class Options(C.Structure):
         ("sort_every", C.c_int), ("cuda_stream", C.c_void_p), ("inner_warm_start", C.c_int),
         ("order", C.c_int), ("refine_max", C.c_int), ("deterministic_deposit", C.c_int),
     ]
+
+
+class CheckpointHeader(C.Structure):
+    """pic_checkpoint_header: the 256-byte head of a checkpoint image."""
+    _fields_ = [
+        ("magic", C.c_char * 8), ("version", C.c_uint32), ("header_bytes", C.c_uint32),
+        ("total_bytes", C.c_uint64), ("checksum", C.c_uint64), ("dim", C.c_int32),
+        ("n", C.c_int32 * 3), ("precision", C.c_int32), ("nspecies", C.c_int32),
+        ("sort_every", C.c_int32), ("reserved0", C.c_int32), ("L", C.c_double * 3),
+        ("x0", C.c_double * 3), ("q", C.c_double * 4), ("m", C.c_double * 4), ("dt", C.c_double),
+        ("E0", C.c_double), ("np", C.c_int64), ("steps_done", C.c_int64),
+        ("reserved", C.c_uint8 * 48),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            if k.startswith("reserved"):
+                continue
+            d[k] = list(v) if hasattr(v, "__len__") and not isinstance(v, bytes) else v
+        return d
+
+
+assert C.sizeof(CheckpointHeader) == 256
 
 
 class Stats(C.Structure):
@@ -110,6 +137,11 @@ def lib():
         L.pic_get_velocities.argtypes = [_VP, _VP, C.c_int]
         L.pic_set_state.argtypes = [_VP, C.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                     _VP, C.c_double, C.c_int]
+        L.pic_checkpoint_bytes.argtypes = [_VP, C.POINTER(C.c_uint64)]
+        L.pic_checkpoint_save.argtypes = [_VP, _VP, C.c_uint64]
+        L.pic_checkpoint_inspect.argtypes = [_VP, C.c_uint64, C.POINTER(CheckpointHeader),
+                                             C.c_char_p, C.c_int]
+        L.pic_checkpoint_load.argtypes = [_VP, _VP, C.c_uint64]
         L.pic_get_stats.argtypes = [_VP, C.POINTER(Stats)]
         L.pic_reset_stats.argtypes = [_VP]
         L.pic_fma_throughput.argtypes = [C.c_int, C.POINTER(C.c_double)]
@@ -141,6 +173,22 @@ def default_options() -> Options:
     o = Options()
     lib().pic_default_options(C.byref(o))
     return o
+
+
+def inspect_checkpoint(image) -> dict:
+    """Validate a checkpoint image (bytes, or a path to a file holding one) on
+    the host and return its header; raises PicError(PIC_EARG) with the reason
+    when the image is damaged or not an image.  Needs no GPU."""
+    if isinstance(image, (str, os.PathLike)):
+        with open(image, "rb") as f:
+            image = f.read()
+    buf = np.frombuffer(image, np.uint8)
+    h = CheckpointHeader()
+    why = C.create_string_buffer(256)
+    rc = lib().pic_checkpoint_inspect(C.c_void_p(buf.ctypes.data), buf.size, C.byref(h), why, 256)
+    if rc:
+        raise PicError(rc, why.value.decode())
+    return h.as_dict()
 
 
 class PicError(RuntimeError):
@@ -345,6 +393,34 @@ class Simulation:
                                         *[_ptr(fields[k], on_device) for k in
                                           ("phi", "psi", "A", "U", "rho", "J")],
                                         float(E0), int(on_device)))
+
+    # -- checkpoint / exact resume (pic_checkpoint_*) -------------------------
+    def checkpoint(self) -> bytes:
+        """The accepted state as a checkpoint image (header + raw sections)."""
+        nb = C.c_uint64()
+        self._check(lib().pic_checkpoint_bytes(self._h, C.byref(nb)))
+        buf = np.empty(nb.value, np.uint8)
+        self._check(lib().pic_checkpoint_save(self._h, C.c_void_p(buf.ctypes.data), nb.value))
+        return buf.tobytes()
+
+    def restore(self, image: bytes):
+        """Replace the state with a checkpoint image from a context of the
+        same mesh, precision and species."""
+        buf = np.frombuffer(image, np.uint8)
+        self._check(lib().pic_checkpoint_load(self._h, C.c_void_p(buf.ctypes.data), buf.size))
+
+    def save_checkpoint(self, path):
+        """Write the checkpoint image to a file (through a temporary name, so
+        an interrupted write never leaves a partial image under `path`)."""
+        data = self.checkpoint()
+        tmp = f"{os.fspath(path)}.tmp{os.getpid()}"
+        with open(tmp, "wb") as f:
+            f.write(data)
+        os.replace(tmp, path)
+
+    def load_checkpoint(self, path):
+        with open(path, "rb") as f:
+            self.restore(f.read())
 
     def stats(self) -> dict:
         st = Stats()

@@ -24,6 +24,7 @@
 // lambda, then the push's derivatives (one dual push per gathered quantity)
 // and the scatters (FP64 atomics).
 #include "map_device.cuh"
+#include "trace.cuh"
 
 #include <cmath>
 #include <string>
@@ -373,6 +374,7 @@ __global__ void k_zip_rec(const double *__restrict__ a, Dual *__restrict__ out, 
 extern "C" int pic_eval_map_vjp(pic_ctx *ctx, const double *j, const double *ybar, double tol,
                                 double *H, double *jbar, int on_device) {
   if (!ctx || !j || !ybar) return PIC_EARG;
+  TraceRange trace("pic_eval_map_vjp");
   if (!ctx->started) {
     ctx->err = "pic_eval_map_vjp before pic_start";
     return PIC_ESTATE;

@@ -39,6 +39,7 @@
 // Per-instance initial states (pic_start) are prepared by a temporary
 // single-problem context per distinct grid and copied in.
 #include "map_device.cuh"
+#include "trace.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -1857,6 +1858,7 @@ int pic_batch_start(pic_batch *bt, pic_report *reports) {
 
 int pic_batch_step(pic_batch *bt, double tol, pic_report *reports) {
   if (!bt) return PIC_EARG;
+  TraceRange trace("pic_batch_step");
   if (!bt->started) {
     bt->err = "pic_batch_step before pic_batch_start";
     return PIC_ESTATE;

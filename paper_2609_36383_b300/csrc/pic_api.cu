@@ -9,6 +9,7 @@
 // outer iteration (accept / backtrack / restart) and solves the <= 8 x 8
 // regularised Gram system of the Anderson update.
 #include "pic_internal.cuh"
+#include "trace.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -247,6 +248,7 @@ int eval_launch(pic_ctx *ctx, const double *jdev, double *Hdev, double *rdev,
 // One evaluation: queue it, wait once, read the counters and the test sums.
 int eval_map(pic_ctx *ctx, const double *jdev, double *Hdev, double *rdev, const StepConst &sc,
              int final_pass, double tr, double ta, Eval *ev, Tests *t) {
+  TraceRange trace(final_pass ? "map_eval_verify" : "map_eval");
   int e;
   if ((e = eval_launch(ctx, jdev, Hdev, rdev, sc, final_pass, tr, ta))) return e;
   CK(cudaStreamSynchronize(ctx->st));
@@ -513,6 +515,7 @@ int pic_set_potentials(pic_ctx *ctx, const double *A, const double *U, int on_de
 
 int pic_start(pic_ctx *ctx, pic_report *out) {
   if (!ctx) return PIC_EARG;
+  TraceRange trace("pic_start");
   tangent_free(ctx);
   const int Ng = ctx->g.Ng;
   int e;
@@ -594,6 +597,7 @@ int pic_eval_map(pic_ctx *ctx, const double *j, double tol, double *H, double *v
 
 int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
   if (!ctx) return PIC_EARG;
+  TraceRange trace("pic_step");
   pic_report R;
   std::memset(&R, 0, sizeof R);
   if (!ctx->started) {
@@ -620,6 +624,7 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
   int mh = 0, hist0 = 0;
   bool done = false;
   for (int k = 0; status == PIC_OK && k < ctx->opt.outer_max; k++) {
+    TraceRange trace_k("outer_iteration");
     R.outer_iters = k + 1;
     R.res_scaled_rms = T.srms;
     R.res_scaled_max = T.smax;
@@ -720,6 +725,7 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
   // keep the device buffers in their named slots for the next step
   ctx->j = j; ctx->H = H; ctx->r = r; ctx->jt = jt; ctx->Ht = Ht; ctx->rt = rt;
   if (status == PIC_OK) {
+    TraceRange trace_c("commit");
     double mesh_work;
     if ((e = field_mesh_work_real(ctx, H, &mesh_work))) return e;
     R.work_residual = ctx->dt * (ev.work_p - mesh_work);

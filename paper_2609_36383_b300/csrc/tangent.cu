@@ -22,6 +22,7 @@
 // differentiate through their moving piece ends, and the deposit carries
 // q (vbar Sbar)' / dV into a second current array.
 #include "map_device.cuh"
+#include "trace.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -269,6 +270,7 @@ bool tangent_supported(pic_ctx *ctx, const char *what) {
 extern "C" int pic_eval_map_jvp(pic_ctx *ctx, const double *j, const double *dj, double tol,
                                 double *H, double *dH, int on_device) {
   if (!ctx || !j || !dj) return PIC_EARG;
+  TraceRange trace("pic_eval_map_jvp");
   if (!ctx->started) {
     ctx->err = "pic_eval_map_jvp before pic_start";
     return PIC_ESTATE;
@@ -451,6 +453,7 @@ double norm2(pic_ctx *ctx, const double *a, int *err) {
 // host by Givens rotations.  Every restart ends with the true residual
 // T(x) - x, so that the last tangent evaluation is the one at x.
 int tangent_solve(pic_ctx *ctx, const StepConst &sc, double tol) {
+  TraceRange trace("tangent_solve");
   TangentState &t = *ctx->tan;
   const size_t N3 = (size_t)3 * ctx->g.Ng;
   const KConst<Dual> kc = kconst<Dual>(sc, pgeom(ctx));
