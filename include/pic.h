@@ -202,16 +202,41 @@ int pic_eval_map_jvp(pic_ctx *ctx, const double *j, const double *dj, double tol
 int pic_eval_map_vjp(pic_ctx *ctx, const double *j, const double *ybar, double tol,
                      double *H, double *jbar, int on_device);
 
+/* The adjoint of one implicit step (reverse mode): given the cotangents of
+   the state after the step, Sbar' = (xbar', Pbar', fbar'), the cotangents of
+   the state before it, Sbar = (dS'/dS)^T Sbar'.  The state is what
+   pic_get_particles and pic_get_potentials return: absolute positions x
+   (dim*N, load order), canonical momenta P (3*N, load order), and the
+   real-space potentials packed as fbar = [phi (Ng), psi (Ng), A (3*Ng),
+   U (3*Ng), rho (Ng)] (9*Ng).  The step's fixed point j* = H(j*, S) is
+   differentiated implicitly: Sbar = G_S^T Sbar' + H_S^T lambda with
+   (I - H_j^T) lambda = G_j^T Sbar', where G commits the particles and the
+   field step; lambda by restarted GMRES(20) to relative residual
+   max(tol, 1e-12) (*gmres_iters receives the operator applications; may be
+   NULL).  The call recomputes the step from the current state (pic_step at
+   tol, orbits recomputed in the backward pass) and leaves the state
+   unchanged; a forward sensitivity (pic_tangent_begin) is dropped.  Input
+   cotangents may be NULL (zero); outputs may be NULL (not wanted).  Chain
+   calls over a run's saved checkpoint images (pic_checkpoint_save), last
+   step first, for the gradient of a function of the final state with
+   respect to the initial one.  FP64, quadratic shapes, no refinement, cold
+   inner start only (PIC_EARG otherwise); PIC_EINNER / PIC_EOUTER if the
+   step or the adjoint solve fails.  The paper differentiates nothing. */
+int pic_step_vjp(pic_ctx *ctx, double tol, const double *xbar1, const double *Pbar1,
+                 const double *fbar1, double *xbar0, double *Pbar0, double *fbar0,
+                 int *gmres_iters, int on_device);
+
 /* Autotuner of the counting-sort interval (sort_every): from the current
    accepted state, each of the ncand candidate intervals (>= 0; 0 = never
    sort) runs `steps` implicit steps at tolerance tol, timed with CUDA events
-   on the context's stream; the state is then restored (particles in load
-   order, sorted once if the chosen interval is positive, as pic_start sorts
-   them), sort_every is set to the fastest candidate and returned in *best.
-   ms_per_step (ncand entries, may be NULL) receives each candidate's time.
-   The statistics of pic_get_stats exclude the tuning steps.  The checkpoint
-   passes through host memory (pic_get_particles / pic_get_potentials /
-   pic_set_state), so a forward sensitivity (pic_tangent_begin) is dropped.
+   on the context's stream, each starting from the same checkpoint image
+   (pic_checkpoint_save, held in host memory), with the particles sorted by
+   cell first when the candidate sorts; then the image is loaded again, so
+   the state is exactly the one before the call (same bits, particle order
+   and step count), sort_every is set to the fastest candidate and returned
+   in *best.  ms_per_step (ncand entries, may be NULL) receives each
+   candidate's time.  The statistics of pic_get_stats exclude the tuning
+   steps.  A forward sensitivity (pic_tangent_begin) is dropped.
    The paper has no autotuner; the interval trades the sort's cost against
    the gathers' locality.  A failing step returns its code with the state
    restored and sort_every unchanged. */

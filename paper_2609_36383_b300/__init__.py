@@ -25,7 +25,7 @@ PIC_FP64, PIC_MIXED = 0, 1
 
 # every symbol include/pic.h declares (checked by the CPU test suite)
 EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
-           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_eval_map_vjp", "pic_tune_sort",
+           "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_eval_map_vjp", "pic_step_vjp", "pic_tune_sort",
            "pic_tangent_begin", "pic_tangent_end", "pic_get_tangent", "pic_num_particles", "pic_get_particles",
            "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_checkpoint_bytes",
            "pic_checkpoint_save", "pic_checkpoint_inspect", "pic_checkpoint_load",
@@ -125,6 +125,8 @@ def lib():
         L.pic_eval_map.argtypes = [_VP, _VP, C.c_double, _VP, _VP, _VP, _VP, C.c_int]
         L.pic_eval_map_jvp.argtypes = [_VP, _VP, _VP, C.c_double, _VP, _VP, C.c_int]
         L.pic_eval_map_vjp.argtypes = [_VP, _VP, _VP, C.c_double, _VP, _VP, C.c_int]
+        L.pic_step_vjp.argtypes = [_VP, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP,
+                                   C.POINTER(C.c_int), C.c_int]
         L.pic_tune_sort.argtypes = [_VP, C.c_double, C.c_int, _VP, C.c_int, C.POINTER(C.c_int),
                                     _VP]
         L.pic_tangent_begin.argtypes = [_VP, _VP, _VP, _VP, C.c_int]
@@ -393,6 +395,76 @@ class Simulation:
                                         *[_ptr(fields[k], on_device) for k in
                                           ("phi", "psi", "A", "U", "rho", "J")],
                                         float(E0), int(on_device)))
+
+    # -- adjoint of a step (pic_step_vjp) --------------------------------------
+    FIELD_ORDER = ("phi", "psi", "A", "U", "rho")
+
+    def _pack_fields(self, f):
+        """{phi, psi, A, U, rho} (missing = zero) -> the 9 Ng array of pic_step_vjp."""
+        N = self.Ng
+        out = np.zeros(9 * N)
+        off = 0
+        for k, nc in zip(self.FIELD_ORDER, (1, 1, 3, 3, 1)):
+            if f is not None and f.get(k) is not None:
+                out[off:off + nc * N] = np.asarray(f[k], np.float64).reshape(-1)
+            off += nc * N
+        return out
+
+    def _unpack_fields(self, a):
+        N = self.Ng
+        out, off = {}, 0
+        for k, nc in zip(self.FIELD_ORDER, (1, 1, 3, 3, 1)):
+            out[k] = a[off:off + nc * N].copy()
+            off += nc * N
+        return out
+
+    def step_vjp(self, tol, xbar=None, Pbar=None, fbar=None) -> dict:
+        """Cotangents of the state before a step from those after it.
+
+        xbar (dim x N), Pbar (3 x N) in load order and fbar (a dict of
+        phi, psi, A, U, rho in real space, as :meth:`fields` returns them)
+        are the cotangents of the state after one step at ``tol``; missing
+        ones are zero.  Returns the cotangents of the current state in the
+        same form (keys ``x``, ``P``, ``fields``) and ``gmres_iters``.  The
+        state is left unchanged."""
+        n = self.num_particles()
+        x1 = None if xbar is None else np.ascontiguousarray(xbar, np.float64).reshape(self.dim, n)
+        P1 = None if Pbar is None else np.ascontiguousarray(Pbar, np.float64).reshape(3, n)
+        f1 = self._pack_fields(fbar) if fbar is not None else None
+        x0 = np.zeros((self.dim, n))
+        P0 = np.zeros((3, n))
+        f0 = np.zeros(9 * self.Ng)
+        its = C.c_int(0)
+        self._check(lib().pic_step_vjp(self._h, float(tol), _ptr(x1, 0), _ptr(P1, 0), _ptr(f1, 0),
+                                       _ptr(x0, 0), _ptr(P0, 0), _ptr(f0, 0), C.byref(its), 0))
+        return {"x": x0, "P": P0, "fields": self._unpack_fields(f0), "gmres_iters": its.value}
+
+    def run_adjoint(self, tol, steps, xbar=None, Pbar=None, fbar=None):
+        """Reverse-mode gradient through ``steps`` steps from the current state.
+
+        Runs the steps forward, keeping each step's checkpoint image on the
+        host, then chains :meth:`step_vjp` from the last step back to the
+        first.  The cotangents given are those of the final state; the
+        result holds the cotangents of the current (initial) state and the
+        forward reports.  The context ends in the final state."""
+        images, reports = [], []
+        for _ in range(steps):
+            images.append(self.checkpoint())
+            r = self.step(tol)
+            if r["status"] != 0:
+                raise PicError(r["status"], "forward step failed")
+            reports.append(r)
+        final = self.checkpoint()
+        g = {"x": xbar, "P": Pbar, "fields": fbar}
+        its = []
+        for img in reversed(images):
+            self.restore(img)
+            g = self.step_vjp(tol, g["x"], g["P"], g["fields"])
+            its.append(g["gmres_iters"])
+        self.restore(final)
+        g["gmres_iters"] = its[::-1]
+        g["reports"] = reports
+        return g
 
     # -- checkpoint / exact resume (pic_checkpoint_*) -------------------------
     def checkpoint(self) -> bytes:

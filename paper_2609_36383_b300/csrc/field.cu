@@ -302,6 +302,73 @@ __global__ void k_cn_adjoint(const double2 *__restrict__ sbar, double2 *__restri
         cscale(scale, cadd(cscale(mu * k[e], ks), cscale(gam, sbar[(size_t)(d + e) * Ng + g])));
 }
 
+// Transpose of the whole field step, mode by mode (the adjoint of a step).
+// k_cn_update maps (phi, psi, A, U, rho, j^) of a mode to the next state
+// (phi', psi', A', U', rho') and to the gather spectra (i k_c phi^{1/2},
+// A'); its coefficients are real except for the factors i k, whose
+// transpose under the real inner product of the real-space fields is -i k.
+// ybar holds the cotangents of the next state [phi', psi', A' (3), U' (3),
+// rho'] and rbar those of the gather spectra [i k phi^{1/2} (dim), A' (3)],
+// both as forward transforms of real-space cotangents; out receives
+// [phi, psi, A (3), U (3), rho, j^ (3)] times scale.  The 2 x 3 matrix of
+// cn_mode is read off cn_mode itself (it is linear), so the transpose uses
+// the forward step's own coefficients.
+__global__ void k_cn_state_adjoint(const double2 *__restrict__ ybar,
+                                   const double2 *__restrict__ rbar, double2 *__restrict__ out,
+                                   SpecGeom sg, double dt, double kap2, double sigma1,
+                                   double sigma2, double scale) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= sg.Ng) return;
+  const int Ng = sg.Ng, d = sg.dim;
+  const double2 z = make_double2(0.0, 0.0);
+  double k[3];
+  const bool nyq = mode_symbols(sg, g, k);
+  if (nyq && sg.project) {  // the forward step zeroes every output of the mode
+    for (int c = 0; c < 12; c++) out[(size_t)c * Ng + g] = z;
+    return;
+  }
+  const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+  const double a = 0.5 * dt, b = 0.5 * dt * kap2 * k2;
+  // cn_mode: (f1, g1) = M (f, g, src) with M real; column q from input e_q
+  double M[2][3];
+  for (int q = 0; q < 3; q++) {
+    const double2 f = make_double2(q == 0 ? 1.0 : 0.0, 0.0);
+    const double2 gg = make_double2(q == 1 ? 1.0 : 0.0, 0.0);
+    const double2 sr = make_double2(q == 2 ? 1.0 : 0.0, 0.0);
+    double2 f1, g1;
+    cn_mode(a, b, f, gg, sr, &f1, &g1);
+    M[0][q] = f1.x;
+    M[1][q] = g1.x;
+  }
+  auto mt = [&](int q, double2 f1b, double2 g1b) {  // row q of M^T (f1b, g1b)
+    return cadd(cscale(M[0][q], f1b), cscale(M[1][q], g1b));
+  };
+  double2 jb[3] = {z, z, z};
+  // vector potential: A' enters the next state and the gather records
+  for (int c = 0; c < 3; c++) {
+    const double2 Ab = cadd(ybar[(size_t)(2 + c) * Ng + g], rbar[(size_t)(d + c) * Ng + g]);
+    const double2 Ub = ybar[(size_t)(5 + c) * Ng + g];
+    out[(size_t)(2 + c) * Ng + g] = cscale(scale, mt(0, Ab, Ub));
+    out[(size_t)(5 + c) * Ng + g] = cscale(scale, mt(1, Ab, Ub));
+    jb[c] = cscale(dt * kap2 * sigma2, mt(2, Ab, Ub));
+  }
+  // scalar potential: phi^{1/2} = (phi + phi') / 2 feeds the records i k phi^{1/2}
+  double2 phb = z;
+  for (int c = 0; c < d; c++) phb = cadd(phb, cmul_i(-k[c], rbar[(size_t)c * Ng + g]));
+  const double2 f1b = cadd(ybar[g], cscale(0.5, phb)), g1b = ybar[(size_t)Ng + g];
+  out[g] = cscale(scale, cadd(cscale(0.5, phb), mt(0, f1b, g1b)));
+  out[(size_t)Ng + g] = cscale(scale, mt(1, f1b, g1b));
+  // source dt kap2 sigma1 rho^{1/2}; rho^{1/2} = rho - (dt/2) div j, rho' = rho - dt div j
+  const double2 rhb = cscale(dt * kap2 * sigma1, mt(2, f1b, g1b));
+  const double2 r1b = ybar[(size_t)8 * Ng + g];
+  out[(size_t)8 * Ng + g] = cscale(scale, cadd(r1b, rhb));
+  const double2 divb = cadd(cscale(-dt, r1b), cscale(-0.5 * dt, rhb));
+  for (int c = 0; c < 3; c++) {
+    jb[c] = cadd(jb[c], cmul_i(-k[c], divb));
+    out[(size_t)(9 + c) * Ng + g] = cscale(scale, jb[c]);
+  }
+}
+
 __global__ void k_constraint_parts(const double2 *phi, const double2 *psi, const double2 *rho,
                                    const double2 *A, const double2 *U, SpecGeom sg,
                                    double sigma1, double inv_kap2, double *out) {
@@ -532,6 +599,15 @@ int field_energy_tangent(pic_ctx *ctx, const SpecState &f, const SpecState &df, 
 int field_cn_adjoint(pic_ctx *ctx, const double2 *sbar, double2 *jbar, double scale) {
   k_cn_adjoint<<<blocks(ctx->g.Ng), kThreads, 0, ctx->st>>>(
       sbar, jbar, spec_geom(ctx), ctx->dt, ctx->opt.kappa * ctx->opt.kappa, ctx->opt.sigma1,
+      ctx->opt.sigma2, scale);
+  KCHECK();
+  return PIC_OK;
+}
+
+int field_cn_state_adjoint(pic_ctx *ctx, const double2 *ybar, const double2 *rbar,
+                           double2 *out, double scale) {
+  k_cn_state_adjoint<<<blocks(ctx->g.Ng), kThreads, 0, ctx->st>>>(
+      ybar, rbar, out, spec_geom(ctx), ctx->dt, ctx->opt.kappa * ctx->opt.kappa, ctx->opt.sigma1,
       ctx->opt.sigma2, scale);
   KCHECK();
   return PIC_OK;

@@ -235,6 +235,13 @@ int field_initial_constraints_into(pic_ctx *ctx, const SpecState &st);
 // jbar^ (3 Ng modes) from the cotangents sbar^ of [i k phi^{1/2} (dim),
 // A^{n+1} (3)], times scale
 int field_cn_adjoint(pic_ctx *ctx, const double2 *sbar, double2 *jbar, double scale);
+// The transpose of the whole field step (adjoint of a step): ybar the 9
+// spectral cotangents of the next state [phi, psi, A (3), U (3), rho], rbar
+// the dim + 3 of the gather spectra [i k phi^{1/2}, A^{n+1}]; out receives
+// 12 spectra [phi, psi, A (3), U (3), rho, j (3)] of the current state and
+// the trial current, times scale.
+int field_cn_state_adjoint(pic_ctx *ctx, const double2 *ybar, const double2 *rbar,
+                           double2 *out, double scale);
 // tangent of the field energy: dW = sum d W / d(phi, A, U) . (dphi, dA, dU)
 int field_energy_tangent(pic_ctx *ctx, const SpecState &st, const SpecState &dst, double *dW);
 int field_energy(pic_ctx *ctx, const double2 *phi_h, const double2 *A_h,

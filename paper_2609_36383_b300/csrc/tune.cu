@@ -30,29 +30,20 @@ extern "C" int pic_tune_sort(pic_ctx *ctx, double tol, int steps, const int *can
   const long long st_l = ctx->launches, st_ml = ctx->map_launches, st_p = ctx->pushes,
                   st_i = ctx->inner_iters, st_pc = ctx->pieces, st_r = ctx->refined;
   const double st_ms = ctx->map_ms;
-  const int64_t n = ctx->np;
-  const int d = ctx->g.dim;
-  const size_t Ng = ctx->g.Ng;
-  // checkpoint of the accepted state (host copies, load order)
-  std::vector<double> x((size_t)d * n), P(3 * (size_t)n), w(n), phi(Ng), psi(Ng), A(3 * Ng),
-      U(3 * Ng), rho(Ng), J(3 * Ng);
-  std::vector<int32_t> sp(n);
+  // exact checkpoint of the accepted state (the device arrays themselves)
+  uint64_t nbytes = 0;
   int e;
-  if ((e = pic_get_particles(ctx, x.data(), P.data(), w.data(), sp.data(), 0))) return e;
-  if ((e = pic_get_potentials(ctx, phi.data(), psi.data(), A.data(), U.data(), rho.data(),
-                              J.data(), 0)))
-    return e;
-  const double E0 = ctx->E0;
-  const long long steps_done = ctx->steps_done;
+  if ((e = pic_checkpoint_bytes(ctx, &nbytes))) return e;
+  std::vector<unsigned char> image(nbytes);
+  if ((e = pic_checkpoint_save(ctx, image.data(), nbytes))) return e;
   const int sort0 = ctx->opt.sort_every;
-  // restore the checkpoint; particles come back in load order and are
-  // sorted once when an interval is set, as pic_start sorts them
-  auto restore = [&](int sort_every) -> int {
-    int r = pic_set_state(ctx, n, sp.data(), x.data(), P.data(), w.data(), phi.data(),
-                          psi.data(), A.data(), U.data(), rho.data(), J.data(), E0, 0);
+  // every candidate starts from the checkpoint, sorted by cell when it sorts
+  // at all (as pic_start leaves the particles)
+  auto restore = [&](int sort_every, bool sort_now) -> int {
+    int r = pic_checkpoint_load(ctx, image.data(), nbytes);
     if (r) return r;
     ctx->opt.sort_every = sort_every;
-    return sort_every > 0 ? particles_sort(ctx) : PIC_OK;
+    return sort_now && sort_every > 0 ? particles_sort(ctx) : PIC_OK;
   };
   cudaEvent_t ea, eb;
   CK(cudaEventCreate(&ea));
@@ -60,7 +51,7 @@ extern "C" int pic_tune_sort(pic_ctx *ctx, double tol, int steps, const int *can
   int best = -1, status = PIC_OK;
   double best_ms = INFINITY;
   for (int k = 0; k < ncand && status == PIC_OK; k++) {
-    if ((status = restore(cand[k]))) break;
+    if ((status = restore(cand[k], true))) break;
     ctx->steps_done = 0;  // every candidate starts in the same phase
     if (cudaEventRecord(ea, ctx->st) != cudaSuccess) {
       status = PIC_ECUDA;
@@ -86,10 +77,9 @@ extern "C" int pic_tune_sort(pic_ctx *ctx, double tol, int steps, const int *can
   }
   cudaEventDestroy(ea);
   cudaEventDestroy(eb);
-  // the state as it was, with the chosen interval; the statistics without
-  // the tuning steps
-  const int r = restore(status == PIC_OK ? best : sort0);
-  ctx->steps_done = steps_done;
+  // the state exactly as it was (same bits, same particle order, same step
+  // count), with the chosen interval; the statistics without the tuning steps
+  const int r = restore(status == PIC_OK ? best : sort0, false);
   ctx->launches = st_l;
   ctx->map_launches = st_ml;
   ctx->pushes = st_p;

@@ -1,0 +1,150 @@
+"""The adjoint of a step (pic_step_vjp) on the CUDA path.
+
+  * One step, 1D/2D/3D: for a random linear functional L = <c, S'> of the
+    state after the step (positions, momenta and all five potentials) and a
+    random direction dS of the state before it, <Sbar, dS> from the adjoint
+    equals the central difference (L(S + h dS) - L(S - h dS)) / 2h, h = 1e-6.
+    The steps converge to tol = 1e-12, so the difference quotient carries
+    about 1e-12 / h = 1e-6 of the state's size as noise; the bound is 1e-5 of
+    the sum of the magnitudes of its terms.
+  * Twenty steps of the 1D two-stream instability, reverse sweep over saved
+    checkpoint images (Simulation.run_adjoint): the gradient with respect to
+    every initial momentum, dotted with the momentum change m du of a drift
+    change du, equals the forward sensitivity (pic_tangent_*) of the same
+    functional in the same direction.  Both are exact derivatives of the
+    discrete step up to the solves' tolerances, so the bound is 1e-8 of the
+    functional's gross size.
+  * The state is unchanged by the call; unsupported contexts are refused.
+"""
+import numpy as np
+import pytest
+
+import paper_2609_36383_b300 as pic
+import pic_inputs
+from tests._common import make_gpu, periodic_diff, small_1d, small_2d
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2609_36383_b300 import build
+    build.build()
+
+
+def _thermal_3d():
+    return pic_inputs.thermal_box(dim=3, n=8, ppc=2, T=0.05, u_drift=0.3, dt=0.2, seed=4)
+
+
+CASES = {"1d_two_stream": small_1d, "2d_weibel": small_2d, "3d_thermal": _thermal_3d}
+TOL = 1e-12
+FIELDS = ("phi", "psi", "A", "U", "rho")
+
+
+def _read(s):
+    x, P, _, _ = s.particles()
+    return x, P, s.fields()
+
+
+def _scale(a):
+    m = np.abs(a).max()
+    return m if m > 0 else 1.0
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_step_adjoint_matches_central_differences(name):
+    cfg = CASES[name]()
+    rng = np.random.default_rng(11)
+    s = make_gpu(cfg)
+    s.start()
+    assert s.step(TOL)["status"] == 0  # a generic state: every potential nonzero
+    x0, P0, w, sp = s.particles()
+    f0 = s.fields()
+    E0 = pic.inspect_checkpoint(s.checkpoint())["E0"]
+    dxc = np.asarray(cfg["L"][:cfg["dim"]], float) / np.asarray(cfg["n"][:cfg["dim"]], float)
+    dx = rng.standard_normal(x0.shape) * dxc[:, None]
+    dP = rng.standard_normal(P0.shape) * _scale(P0)
+    df = {k: rng.standard_normal(f0[k].shape) * _scale(f0[k]) for k in FIELDS}
+    cx = rng.standard_normal(x0.shape)
+    cP = rng.standard_normal(P0.shape)
+    cf = {k: rng.standard_normal(f0[k].shape) for k in FIELDS}
+
+    def load(eps):
+        f = dict(f0)
+        for k in FIELDS:
+            f[k] = f0[k] + eps * df[k]
+        s.set_state(x0 + eps * dx, P0 + eps * dP, w, sp, f, E0)
+
+    load(0.0)
+    img = s.checkpoint()
+    g = s.step_vjp(TOL, cx, cP, cf)
+    assert s.checkpoint() == img  # the state is unchanged
+    lhs_terms = [np.sum(g["x"] * dx), np.sum(g["P"] * dP)] + \
+                [np.sum(g["fields"][k] * df[k]) for k in FIELDS]
+    h = 1e-6
+    out = {}
+    for sgn in (1, -1):
+        load(sgn * h)
+        assert s.step(TOL)["status"] == 0
+        out[sgn] = _read(s)
+    (xp, Pp, fp), (xm, Pm, fm) = out[1], out[-1]
+    fd_terms = [np.sum(cx * periodic_diff(xp, xm, cfg["L"])) / (2 * h),
+                np.sum(cP * (Pp - Pm)) / (2 * h)] + \
+               [np.sum(cf[k] * (fp[k] - fm[k])) / (2 * h) for k in FIELDS]
+    gross = sum(abs(t) for t in fd_terms) + sum(abs(t) for t in lhs_terms)
+    lhs, fd = sum(lhs_terms), sum(fd_terms)
+    print(f"{name}: <Sbar, dS> {lhs:.10e}, central difference {fd:.10e}, "
+          f"|diff| / gross {abs(lhs - fd) / gross:.2e}, GMRES applications {g['gmres_iters']}; "
+          f"terms adjoint {np.array(lhs_terms)}, FD {np.array(fd_terms)}")
+    assert abs(lhs - fd) <= 1e-5 * gross
+
+
+def test_twenty_step_reverse_sweep_matches_the_forward_sensitivity():
+    u0, steps = 0.6, 20
+    mk = lambda u: pic_inputs.two_stream_1d(nx=64, ppc_beam=32, u0=u)
+    cfg = mk(u0)
+    du = (mk(u0 + 1e-6)["u"] - mk(u0 - 1e-6)["u"]) / 2e-6
+    N, Ng = cfg["u"].shape[1], int(np.prod(cfg["n"]))
+    rng = np.random.default_rng(5)
+    cx = rng.standard_normal((cfg["dim"], N))
+    cP = rng.standard_normal((3, N))
+    cA = rng.standard_normal(3 * Ng)
+    cU = rng.standard_normal(3 * Ng)
+    # forward: the tangent of the final state in the direction du
+    s = make_gpu(cfg)
+    s.start()
+    s.tangent_begin(du=du)
+    for _ in range(steps):
+        assert s.step(TOL)["status"] == 0
+    t = s.tangent()
+    fwd_terms = [np.sum(cx * t["dx"]), np.sum(cP * t["dP"]), np.sum(cA * t["dA"]),
+                 np.sum(cU * t["dU"])]
+    # reverse: one sweep gives the gradient with respect to every momentum
+    s2 = make_gpu(cfg)
+    s2.start()
+    g = s2.run_adjoint(TOL, steps, cx, cP, {"A": cA, "U": cU})
+    ms = np.array([m for _, m in cfg["species"]])
+    m_p = cfg["w"] * ms[cfg["sp"]]
+    adj = np.sum(g["P"] * (m_p * du))
+    fwd = sum(fwd_terms)
+    gross = sum(abs(v) for v in fwd_terms)
+    print(f"d<c, S_20>/du0: adjoint {adj:.12e}, forward {fwd:.12e}, |diff| / gross "
+          f"{abs(adj - fwd) / gross:.2e}; GMRES applications per step {g['gmres_iters']}")
+    assert abs(adj - fwd) <= 1e-8 * gross
+    # the sweep leaves the context in the final state, which steps on
+    assert s2.step(TOL)["status"] == 0
+
+
+def test_step_vjp_refuses_unsupported_contexts():
+    cfg = small_2d()
+    s = make_gpu(cfg, precision=pic.PIC_MIXED)
+    s.start()
+    with pytest.raises(pic.PicError) as ei:
+        s.step_vjp(TOL)
+    assert ei.value.code == pic.PIC_EARG
+    t = make_gpu(cfg)
+    with pytest.raises(pic.PicError) as ei:
+        t.step_vjp(TOL)
+    assert ei.value.code == pic.PIC_ESTATE
