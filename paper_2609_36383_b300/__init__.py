@@ -490,6 +490,10 @@ class Simulation:
             f.write(data)
         os.replace(tmp, path)
 
+    def checkpoint_header(self) -> dict:
+        """The header of the current state's checkpoint image (E0, step count, ...)."""
+        return inspect_checkpoint(self.checkpoint())
+
     def load_checkpoint(self, path):
         with open(path, "rb") as f:
             self.restore(f.read())

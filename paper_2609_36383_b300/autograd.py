@@ -12,6 +12,13 @@
   the reverse-mode derivative of this scalar-input function are exact
   products with d(W, K)/d theta.
 
+* ``state_after(sim, tol, steps, x, P, f)``: the state after ``steps``
+  implicit steps from the state (x, P, f) (positions, canonical momenta and
+  the potentials packed as [phi, psi, A, U, rho]), as tensors; its reverse
+  mode is a sweep of ``pic_step_vjp`` over the checkpoint images the forward
+  pass keeps, so one backward pass gives the gradient with respect to every
+  particle and every mesh value.
+
 Argument marshalling only: every derivative is computed by the library.
 """
 from __future__ import annotations
@@ -95,3 +102,76 @@ def energies_after(theta: torch.Tensor, make, seed, steps: int, tol: float) -> t
     condition (any may be omitted)."""
     out, _ = _EnergiesAfter.apply(theta, make, seed, steps, tol)
     return out
+
+
+FIELD_PARTS = (("phi", 1), ("psi", 1), ("A", 3), ("U", 3), ("rho", 1))
+
+
+def pack_fields(f: dict, Ng: int) -> np.ndarray:
+    """{phi, psi, A, U, rho} -> one array of 9 Ng values (that order)."""
+    return np.concatenate([np.asarray(f[k], np.float64).reshape(nc * Ng) for k, nc in FIELD_PARTS])
+
+
+def unpack_fields(a: np.ndarray, Ng: int) -> dict:
+    out, off = {}, 0
+    for k, nc in FIELD_PARTS:
+        out[k] = np.array(a[off:off + nc * Ng], np.float64)
+        off += nc * Ng
+    return out
+
+
+class _StateAfter(torch.autograd.Function):
+    @staticmethod
+    def forward(x, P, f, sim, tol, steps):
+        if steps < 1:
+            raise ValueError("state_after needs at least one step")
+        _, _, w, sp = sim.particles()
+        seed = sim.fields()["J"]
+        E0 = sim.checkpoint_header()["E0"]
+        fields = unpack_fields(f.detach().cpu().numpy(), sim.Ng)
+        fields["J"] = seed
+        sim.set_state(x.detach().cpu().numpy(), P.detach().cpu().numpy(), w, sp, fields, E0)
+        images = []
+        for _ in range(steps):
+            images.append(sim.checkpoint())
+            r = sim.step(tol)
+            if r["status"]:
+                raise RuntimeError(f"step failed with status {r['status']}")
+        x1, P1, _, _ = sim.particles()
+        f1 = pack_fields(sim.fields(), sim.Ng)
+        sim._autograd_images = images  # kept for the backward sweep
+        dev = x.device
+        return (torch.from_numpy(x1).to(dev), torch.from_numpy(P1).to(dev),
+                torch.from_numpy(f1).to(dev))
+
+    @staticmethod
+    def setup_context(ctx, inputs, output):
+        _, _, _, sim, tol, steps = inputs
+        ctx.sim, ctx.tol = sim, tol
+        ctx.images = sim._autograd_images
+        del sim._autograd_images
+
+    @staticmethod
+    def backward(ctx, gx, gP, gf):
+        sim = ctx.sim
+        final = sim.checkpoint()
+        g = {"x": gx.detach().cpu().numpy(), "P": gP.detach().cpu().numpy(),
+             "fields": unpack_fields(gf.detach().cpu().numpy(), sim.Ng)}
+        for img in reversed(ctx.images):
+            sim.restore(img)
+            g = sim.step_vjp(ctx.tol, g["x"], g["P"], g["fields"])
+        sim.restore(final)
+        dev = gx.device
+        return (torch.from_numpy(g["x"]).to(dev), torch.from_numpy(g["P"]).to(dev),
+                torch.from_numpy(pack_fields(g["fields"], sim.Ng)).to(dev), None, None, None)
+
+
+def state_after(sim, tol: float, steps: int, x: torch.Tensor, P: torch.Tensor, f: torch.Tensor):
+    """(x, P, f) after ``steps`` steps of the started FP64 simulation ``sim``
+    from the state (x, P, f); differentiable in all three (reverse mode).
+
+    x: dim x N positions, P: 3 x N canonical momenta (load order), f: the
+    9 Ng potentials [phi, psi, A, U, rho] as ``pack_fields`` packs
+    ``sim.fields()``.  Weights, species and the reference energy are the
+    simulation's own; the simulation is left in the final state."""
+    return _StateAfter.apply(x, P, f, sim, tol, steps)

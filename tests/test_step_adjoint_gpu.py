@@ -148,3 +148,45 @@ def test_step_vjp_refuses_unsupported_contexts():
     with pytest.raises(pic.PicError) as ei:
         t.step_vjp(TOL)
     assert ei.value.code == pic.PIC_ESTATE
+
+
+def test_state_after_autograd_gradient_matches_central_differences():
+    """torch.autograd through two steps (paper_2609_36383_b300.autograd.state_after):
+    the reverse-mode gradient of <c, S_2> with respect to every position,
+    momentum and potential of S_0, dotted with a random direction, equals
+    the central difference of the forward pass."""
+    import torch
+    from paper_2609_36383_b300 import autograd as pa
+    cfg = small_2d()
+    s = make_gpu(cfg)
+    s.start()
+    assert s.step(TOL)["status"] == 0
+    x0, P0, _, _ = s.particles()
+    f0 = pa.pack_fields(s.fields(), s.Ng)
+    base = s.checkpoint()
+    rng = np.random.default_rng(21)
+    dxc = np.asarray(cfg["L"][:2], float) / np.asarray(cfg["n"][:2], float)
+    d = [rng.standard_normal(x0.shape) * dxc[:, None],
+         rng.standard_normal(P0.shape) * _scale(P0),
+         rng.standard_normal(f0.shape) * _scale(f0)]
+    c = [rng.standard_normal(x0.shape), rng.standard_normal(P0.shape),
+         rng.standard_normal(f0.shape)]
+    x, P, f = (torch.tensor(a, requires_grad=True) for a in (x0, P0, f0))
+    out = pa.state_after(s, TOL, 2, x, P, f)
+    loss = sum((torch.from_numpy(ci) * t).sum() for ci, t in zip(c, out))
+    loss.backward()
+    lhs = sum(np.sum(g.grad.numpy() * di) for g, di in zip((x, P, f), d))
+    h = 1e-6
+    res = {}
+    for sg in (1, -1):
+        s.restore(base)
+        with torch.no_grad():
+            res[sg] = [t.numpy() for t in pa.state_after(
+                s, TOL, 2, *(torch.from_numpy(a + sg * h * di) for a, di in zip((x0, P0, f0), d)))]
+    terms = [np.sum(c[0] * periodic_diff(res[1][0], res[-1][0], cfg["L"])) / (2 * h)] + \
+            [np.sum(ci * (res[1][k] - res[-1][k])) / (2 * h) for k, ci in ((1, c[1]), (2, c[2]))]
+    fd = sum(terms)
+    gross = sum(abs(t) for t in terms)
+    print(f"autograd <grad, d> {lhs:.10e}, central difference {fd:.10e}, "
+          f"|diff| / gross {abs(lhs - fd) / gross:.2e}")
+    assert abs(lhs - fd) <= 1e-5 * gross
