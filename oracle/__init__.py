@@ -94,6 +94,8 @@ def lib():
         L.orc_get_particles.argtypes = [C.c_void_p, _D, _D, _D, _I]
         L.orc_get_fields.argtypes = [C.c_void_p, _D, _D, _D, _D, _D, _D]
         L.orc_set_fields.argtypes = [C.c_void_p, _D, _D, _D, _D, _D, _D]
+        L.orc_set_state.argtypes = [C.c_void_p, C.c_long, C.POINTER(C.c_int), _D, _D, _D, _D, _D,
+                                    _D, _D, _D, _D]
         L.orc_S2.restype = C.c_double
         L.orc_S2.argtypes = [C.c_double]
         L.orc_dS2.restype = C.c_double
@@ -295,6 +297,17 @@ class Oracle:
     def set_fields(self, phi=None, psi=None, A=None, U=None, rho=None, J=None):
         vals = [None if v is None else _f64(v) for v in (phi, psi, A, U, rho, J)]
         lib().orc_set_fields(self._h, *[_p(v) for v in vals])
+
+    def set_state(self, x, P, w, species, fields):
+        """A full accepted state (canonical momenta, every mesh array); the
+        context is started and steps on from it."""
+        x = _f64(x); P = _f64(P); w = _f64(w)
+        sp = np.ascontiguousarray(species, np.int32)
+        f = {k: _f64(fields[k]) for k in ("phi", "psi", "A", "U", "rho", "J")}
+        st = lib().orc_set_state(self._h, w.shape[0], _pi(sp), _p(x), _p(P), _p(w),
+                                 *[_p(f[k]) for k in ("phi", "psi", "A", "U", "rho", "J")])
+        if st:
+            raise ValueError(f"orc_set_state: {st}")
 
     # -- unit-level pieces ------------------------------------------------
     def field_solve(self, j):

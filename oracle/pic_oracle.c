@@ -773,6 +773,18 @@ int orc_set_fields(void *h, const double *phi, const double *psi, const double *
   return ORC_OK;
 }
 
+int orc_set_state(void *h, long np, const int *species, const double *x, const double *P,
+                  const double *w, const double *phi, const double *psi, const double *A,
+                  const double *U, const double *rho, const double *J) {
+  orc *o = (orc *)h;
+  int st = orc_set_particles(h, np, species, x, P, 1, w);
+  if (st) return st;
+  orc_set_fields(h, phi, psi, A, U, rho, J);
+  o->pending_mech = 0;
+  o->started = 1;
+  return ORC_OK;
+}
+
 static double pq(const orc *o, long i) { return o->w[i] * o->p.q[o->sp[i]]; }
 static double pm(const orc *o, long i) { return o->w[i] * o->p.m[o->sp[i]]; }
 

@@ -81,6 +81,13 @@ int orc_get_fields(void *h, double *phi, double *psi, double *A, double *U,
 int orc_set_fields(void *h, const double *phi, const double *psi, const double *A,
                    const double *U, const double *rho, const double *J);
 
+/* A full accepted state, as after pic_start or a step (test support, no
+   arithmetic): particles with canonical momenta and every mesh array; the
+   context is then started, so orc_step continues from it. */
+int orc_set_state(void *h, long np, const int *species, const double *x, const double *P,
+                  const double *w, const double *phi, const double *psi, const double *A,
+                  const double *U, const double *rho, const double *J);
+
 /* unit-level pieces, exposed so that tests can pin them one by one */
 double orc_S2(double xi);
 double orc_dS2(double xi);

@@ -485,6 +485,35 @@ def test_failed_step_leaves_state_unchanged(orc):
             assert np.array_equal(fa[k], fc[k])
 
 
+def test_set_state_continues_a_run_exactly(orc):
+    """The oracle's full-state restore (test support for derivative checks):
+    a context given another's accepted state (canonical momenta and every
+    mesh array) takes the same next step, to the last bit."""
+    import oracle as O
+    def make():
+        o = O.Oracle(2, [16, 16], [2 * math.pi] * 2, [-math.pi] * 2, [(-1.0, 1.0)], dt=0.1,
+                     rho_bg=1.0)
+        rng = np.random.default_rng(12)
+        x = rng.uniform(-math.pi, math.pi, (2, 128))
+        u = rng.standard_normal((3, 128)) * 0.3
+        o.set_particles(x, u, np.full(128, 4 * math.pi ** 2 / 128))
+        o.start()
+        return o
+    a = make()
+    assert a.step(1e-12)["status"] == 0
+    x, P, w, sp = a.particles()
+    b = O.Oracle(2, [16, 16], [2 * math.pi] * 2, [-math.pi] * 2, [(-1.0, 1.0)], dt=0.1,
+                 rho_bg=1.0)
+    b.set_state(x, P, w, sp, a.fields())
+    ra, rb = a.step(1e-12), b.step(1e-12)
+    assert ra["status"] == 0 and rb["status"] == 0
+    for u, v in zip(a.particles(), b.particles()):
+        assert np.array_equal(u, v)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
 def test_two_stream_growth_rate_and_energy(orc):
     """1D3V two-stream with u = +-0.6, k = 0.5, dx = pi/16, seeded with the
     growing finite-grid eigenvector (Sec. 5.1): the k = 0.5 mode of E_x grows

@@ -14,6 +14,9 @@
     functional in the same direction.  Both are exact derivatives of the
     discrete step up to the solves' tolerances, so the bound is 1e-8 of the
     functional's gross size.
+  * The same functional and directions against central differences of the
+    FP64 oracle's step (an implementation that shares no code with the CUDA
+    path), with the same bound.
   * The state is unchanged by the call; unsupported contexts are refused.
 """
 import numpy as np
@@ -21,7 +24,7 @@ import pytest
 
 import paper_2609_36383_b300 as pic
 import pic_inputs
-from tests._common import make_gpu, periodic_diff, small_1d, small_2d
+from tests._common import make_gpu, make_oracle, periodic_diff, small_1d, small_2d
 
 pytestmark = pytest.mark.gpu
 
@@ -98,6 +101,49 @@ def test_step_adjoint_matches_central_differences(name):
     print(f"{name}: <Sbar, dS> {lhs:.10e}, central difference {fd:.10e}, "
           f"|diff| / gross {abs(lhs - fd) / gross:.2e}, GMRES applications {g['gmres_iters']}; "
           f"terms adjoint {np.array(lhs_terms)}, FD {np.array(fd_terms)}")
+    assert abs(lhs - fd) <= 1e-5 * gross
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_step_adjoint_matches_oracle_central_differences(name):
+    import oracle
+    oracle.build()
+    cfg = CASES[name]()
+    rng = np.random.default_rng(13)
+    s = make_gpu(cfg)
+    s.start()
+    assert s.step(TOL)["status"] == 0
+    x0, P0, w, sp = s.particles()
+    f0 = s.fields()
+    E0 = pic.inspect_checkpoint(s.checkpoint())["E0"]
+    dxc = np.asarray(cfg["L"][:cfg["dim"]], float) / np.asarray(cfg["n"][:cfg["dim"]], float)
+    dx = rng.standard_normal(x0.shape) * dxc[:, None]
+    dP = rng.standard_normal(P0.shape) * _scale(P0)
+    df = {k: rng.standard_normal(f0[k].shape) * _scale(f0[k]) for k in FIELDS}
+    cx = rng.standard_normal(x0.shape)
+    cP = rng.standard_normal(P0.shape)
+    cf = {k: rng.standard_normal(f0[k].shape) for k in FIELDS}
+    s.set_state(x0, P0, w, sp, f0, E0)
+    g = s.step_vjp(TOL, cx, cP, cf)
+    lhs = np.sum(g["x"] * dx) + np.sum(g["P"] * dP) + \
+        sum(np.sum(g["fields"][k] * df[k]) for k in FIELDS)
+    o = make_oracle(cfg)
+    h = 1e-6
+    out = {}
+    for sgn in (1, -1):
+        f = {k: f0[k] + sgn * h * df[k] for k in FIELDS}
+        f["J"] = f0["J"]
+        o.set_state(x0 + sgn * h * dx, P0 + sgn * h * dP, w, sp, f)
+        assert o.step(TOL)["status"] == 0
+        xo, Po, _, _ = o.particles()
+        out[sgn] = (xo, Po, o.fields())
+    (xp, Pp, fp), (xm, Pm, fm) = out[1], out[-1]
+    terms = [np.sum(cx * periodic_diff(xp, xm, cfg["L"])) / (2 * h),
+             np.sum(cP * (Pp - Pm)) / (2 * h)] + \
+            [np.sum(cf[k] * (fp[k] - fm[k])) / (2 * h) for k in FIELDS]
+    fd, gross = sum(terms), sum(abs(t) for t in terms)
+    print(f"{name}: GPU adjoint {lhs:.10e}, oracle central difference {fd:.10e}, "
+          f"|diff| / gross {abs(lhs - fd) / gross:.2e}")
     assert abs(lhs - fd) <= 1e-5 * gross
 
 
