@@ -229,9 +229,10 @@ int pic_step_vjp(pic_ctx *ctx, double tol, const double *xbar1, const double *Pb
 /* Autotuner of the counting-sort interval (sort_every): from the current
    accepted state, each of the ncand candidate intervals (>= 0; 0 = never
    sort) runs `steps` implicit steps at tolerance tol, timed with CUDA events
-   on the context's stream, each starting from the same checkpoint image
-   (pic_checkpoint_save, held in host memory), with the particles sorted by
-   cell first when the candidate sorts; then the image is loaded again, so
+   on the context's stream, each starting from the same snapshot of the
+   state (the checkpoint image's content, held in device memory), with the
+   particles sorted by cell first when the candidate sorts; then the
+   snapshot is restored, so
    the state is exactly the one before the call (same bits, particle order
    and step count), sort_every is set to the fastest candidate and returned
    in *best.  ms_per_step (ncand entries, may be NULL) receives each

@@ -226,7 +226,71 @@ void mesh_sections(pic_ctx *ctx, MeshSec out[7]) {
   out[6] = {ctx->J_acc, 24 * g};
 }
 
+// Copies between the context's state and an image buffer laid out as the
+// checkpoint image (header bytes untouched); `to_image` selects the
+// direction, `kind` host or device memory on the image side.
+int image_copy(pic_ctx *ctx, unsigned char *b, bool to_image, bool image_on_device) {
+  const int d = ctx->g.dim;
+  const uint64_t R = ctx->rsize, n = ctx->np, cap = ctx->cap;
+  const Layout L = layout(d, (int)R, ctx->np, ctx->g.Ng);
+  const cudaMemcpyKind k = to_image ? (image_on_device ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyDeviceToHost)
+                                    : (image_on_device ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice);
+  auto cp = [&](void *dev, uint64_t off, uint64_t bytes) -> int {
+    if (bytes == 0) return PIC_OK;
+    if (to_image) CK(cudaMemcpyAsync(b + off, dev, bytes, k, ctx->st));
+    else CK(cudaMemcpyAsync(dev, b + off, bytes, k, ctx->st));
+    return PIC_OK;
+  };
+  int e;
+  for (int l = 0; l < d; l++) {
+    if ((e = cp(ctx->cell + l * cap, L.off[Layout::CELL] + 4 * l * n, 4 * n))) return e;
+    if ((e = cp((char *)ctx->off + R * l * cap, L.off[Layout::OFF] + R * l * n, R * n))) return e;
+  }
+  for (int c = 0; c < 3; c++)
+    if ((e = cp((char *)ctx->P + R * c * cap, L.off[Layout::P] + R * c * n, R * n))) return e;
+  if ((e = cp(ctx->w, L.off[Layout::W], 8 * n))) return e;
+  if ((e = cp(ctx->sp, L.off[Layout::SP], 4 * n))) return e;
+  if ((e = cp(ctx->id, L.off[Layout::ID], 8 * n))) return e;
+  MeshSec ms[7];
+  mesh_sections(ctx, ms);
+  for (int q = 0; q < 7; q++)
+    if ((e = cp(ms[q].dev, L.off[Layout::PHI + q], ms[q].bytes))) return e;
+  return PIC_OK;
+}
+
 }  // namespace
+
+// A device-side snapshot of the accepted state in the image layout (no
+// header, no checksum, no validation: the library's own data), and its
+// restore into the same context with the same particle count; for calls
+// that run a step and must put the state back (pic_step_vjp).
+uint64_t state_snapshot_bytes(const pic_ctx *ctx) {
+  return layout(ctx->g.dim, ctx->rsize, ctx->np, ctx->g.Ng).off[Layout::NSEC];
+}
+
+int state_snapshot(pic_ctx *ctx, void *dev) {
+  return image_copy(ctx, (unsigned char *)dev, true, true);
+}
+
+int state_restore(pic_ctx *ctx, const void *dev, int64_t np, long long steps_done,
+                  int sort_every, double E0) {
+  if (np != ctx->np) {
+    ctx->err = "state_restore: particle count changed";
+    return PIC_EARG;
+  }
+  tangent_free(ctx);
+  graphs_clear(ctx);
+  int e;
+  if ((e = image_copy(ctx, (unsigned char *)const_cast<void *>(dev), false, true))) return e;
+  if ((e = particles_refresh_A(ctx))) return e;
+  ctx->E0 = E0;
+  ctx->steps_done = steps_done;
+  ctx->opt.sort_every = sort_every;
+  ctx->started = 1;
+  return PIC_OK;
+}
 
 extern "C" {
 
@@ -243,35 +307,15 @@ int pic_checkpoint_save(pic_ctx *ctx, void *image, uint64_t bytes) {
     return PIC_ESTATE;
   }
   TraceRange tr("pic_checkpoint_save");
-  const int d = ctx->g.dim;
-  const uint64_t R = ctx->rsize, n = ctx->np, cap = ctx->cap;
-  const Layout L = layout(d, (int)R, ctx->np, ctx->g.Ng);
+  const Layout L = layout(ctx->g.dim, ctx->rsize, ctx->np, ctx->g.Ng);
   if (bytes != L.off[Layout::NSEC]) {
     ctx->err = "pic_checkpoint_save: buffer size differs from pic_checkpoint_bytes";
     return PIC_EARG;
   }
   unsigned char *b = (unsigned char *)image;
   std::memset(b, 0, bytes);  // section padding is part of the checksum
-  const cudaMemcpyKind D2H = cudaMemcpyDeviceToHost;
-  // particle rows are stored with stride cap on the device, np in the image
-  for (int l = 0; l < d && n > 0; l++) {
-    CK(cudaMemcpyAsync(b + L.off[Layout::CELL] + 4 * l * n, ctx->cell + l * cap, 4 * n, D2H,
-                       ctx->st));
-    CK(cudaMemcpyAsync(b + L.off[Layout::OFF] + R * l * n, (char *)ctx->off + R * l * cap, R * n,
-                       D2H, ctx->st));
-  }
-  for (int c = 0; c < 3 && n > 0; c++)
-    CK(cudaMemcpyAsync(b + L.off[Layout::P] + R * c * n, (char *)ctx->P + R * c * cap, R * n, D2H,
-                       ctx->st));
-  if (n > 0) {
-    CK(cudaMemcpyAsync(b + L.off[Layout::W], ctx->w, 8 * n, D2H, ctx->st));
-    CK(cudaMemcpyAsync(b + L.off[Layout::SP], ctx->sp, 4 * n, D2H, ctx->st));
-    CK(cudaMemcpyAsync(b + L.off[Layout::ID], ctx->id, 8 * n, D2H, ctx->st));
-  }
-  MeshSec ms[7];
-  mesh_sections(ctx, ms);
-  for (int s = 0; s < 7; s++)
-    CK(cudaMemcpyAsync(b + L.off[Layout::PHI + s], ms[s].dev, ms[s].bytes, D2H, ctx->st));
+  int e;
+  if ((e = image_copy(ctx, b, true, false))) return e;
   CK(cudaStreamSynchronize(ctx->st));
   pic_checkpoint_header h = header_of(ctx);
   h.total_bytes = bytes;
@@ -320,34 +364,13 @@ int pic_checkpoint_load(pic_ctx *ctx, const void *image, uint64_t bytes) {
   int e;
   if ((e = particles_alloc(ctx, h.np))) return e;
   ctx->np = h.np;
-  const int d = h.dim;
+  // rows of ignorable dimensions are never read; keep them defined
   const uint64_t R = ctx->rsize, n = h.np, cap = ctx->cap;
-  const Layout L = layout(d, (int)R, h.np, ctx->g.Ng);
-  const unsigned char *b = (const unsigned char *)image;
-  const cudaMemcpyKind H2D = cudaMemcpyHostToDevice;
-  for (int l = 0; l < 3 && n > 0; l++) {
-    if (l < d) {
-      CK(cudaMemcpyAsync(ctx->cell + l * cap, b + L.off[Layout::CELL] + 4 * l * n, 4 * n, H2D,
-                         ctx->st));
-      CK(cudaMemcpyAsync((char *)ctx->off + R * l * cap, b + L.off[Layout::OFF] + R * l * n,
-                         R * n, H2D, ctx->st));
-    } else {  // rows of ignorable dimensions are never read; keep them defined
-      CK(cudaMemsetAsync(ctx->cell + l * cap, 0, 4 * n, ctx->st));
-      CK(cudaMemsetAsync((char *)ctx->off + R * l * cap, 0, R * n, ctx->st));
-    }
+  for (int l = h.dim; l < 3 && n > 0; l++) {
+    CK(cudaMemsetAsync(ctx->cell + l * cap, 0, 4 * n, ctx->st));
+    CK(cudaMemsetAsync((char *)ctx->off + R * l * cap, 0, R * n, ctx->st));
   }
-  for (int c = 0; c < 3 && n > 0; c++)
-    CK(cudaMemcpyAsync((char *)ctx->P + R * c * cap, b + L.off[Layout::P] + R * c * n, R * n, H2D,
-                       ctx->st));
-  if (n > 0) {
-    CK(cudaMemcpyAsync(ctx->w, b + L.off[Layout::W], 8 * n, H2D, ctx->st));
-    CK(cudaMemcpyAsync(ctx->sp, b + L.off[Layout::SP], 4 * n, H2D, ctx->st));
-    CK(cudaMemcpyAsync(ctx->id, b + L.off[Layout::ID], 8 * n, H2D, ctx->st));
-  }
-  MeshSec ms[7];
-  mesh_sections(ctx, ms);
-  for (int s = 0; s < 7; s++)
-    CK(cudaMemcpyAsync(ms[s].dev, b + L.off[Layout::PHI + s], ms[s].bytes, H2D, ctx->st));
+  if ((e = image_copy(ctx, (unsigned char *)const_cast<void *>(image), false, false))) return e;
   if ((e = particles_refresh_A(ctx))) return e;
   if ((e = det_alloc(ctx))) return e;
   CK(cudaStreamSynchronize(ctx->st));

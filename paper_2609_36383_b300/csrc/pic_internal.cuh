@@ -242,6 +242,15 @@ int field_cn_adjoint(pic_ctx *ctx, const double2 *sbar, double2 *jbar, double sc
 // the trial current, times scale.
 int field_cn_state_adjoint(pic_ctx *ctx, const double2 *ybar, const double2 *rbar,
                            double2 *out, double scale);
+
+// ---------------------------------------------------------------- checkpoint.cu
+// A device-side snapshot of the accepted state in the checkpoint image's
+// layout (no header, no validation), and its restore into the same context
+// with the same particle count (drops a forward sensitivity).
+uint64_t state_snapshot_bytes(const pic_ctx *ctx);
+int state_snapshot(pic_ctx *ctx, void *dev);
+int state_restore(pic_ctx *ctx, const void *dev, int64_t np, long long steps_done,
+                  int sort_every, double E0);
 // tangent of the field energy: dW = sum d W / d(phi, A, U) . (dphi, dA, dU)
 int field_energy_tangent(pic_ctx *ctx, const SpecState &st, const SpecState &dst, double *dW);
 int field_energy(pic_ctx *ctx, const double2 *phi_h, const double2 *A_h,

@@ -26,9 +26,9 @@
 // solved by restarted GMRES on the j-part of the generalised VJP.
 //
 // The call recomputes the step (orbits are recomputed, nothing is stored by
-// the forward run): it saves the exact state image, runs pic_step for j*,
-// loads the image back, and differentiates at (j*, S^n).  The context's
-// state is unchanged on return.
+// the forward run): it snapshots the state on the device, runs pic_step for
+// j*, copies the snapshot back, and differentiates at (j*, S^n).  The
+// context's state is unchanged on return.
 #include "adjoint_device.cuh"
 #include "trace.cuh"
 
@@ -628,11 +628,18 @@ extern "C" int pic_step_vjp(pic_ctx *ctx, double tol, const double *xbar1, const
   const int d = ctx->g.dim, Ng = ctx->g.Ng, nvp = node_record_len(d);
   const size_t N3 = (size_t)3 * Ng;
   int e;
-  // 1. the step itself, for j*; the exact state image brings S^n back
-  uint64_t nbytes = 0;
-  if ((e = pic_checkpoint_bytes(ctx, &nbytes))) return e;
-  std::vector<unsigned char> image(nbytes);
-  if ((e = pic_checkpoint_save(ctx, image.data(), nbytes))) return e;
+  // 1. the step itself, for j*; a device snapshot of the state brings S^n back
+  struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+      if (p) cudaFree(p);
+    }
+  } snap;
+  CK(cudaMalloc(&snap.p, state_snapshot_bytes(ctx)));
+  if ((e = state_snapshot(ctx, snap.p))) return e;
+  const long long steps0 = ctx->steps_done;
+  const int sort0 = ctx->opt.sort_every;
+  const double E00 = ctx->E0;
   pic_report rep;
   const int st_step = pic_step(ctx, tol, &rep);
   if (st_step != PIC_OK) return st_step;  // a failed step leaves S^n in place
@@ -669,7 +676,7 @@ extern "C" int pic_step_vjp(pic_ctx *ctx, double tol, const double *xbar1, const
          *ptmp = Pb0s + 3 * cap;  // 3 x np rows in load order
   CK(cudaMemcpyAsync(jstar, ctx->J_acc, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
-  if ((e = pic_checkpoint_load(ctx, image.data(), nbytes))) return e;
+  if ((e = state_restore(ctx, snap.p, np, steps0, sort0, E00))) return e;
   // 2. the map evaluation at (j*, S^n): records, then vbar and its Jacobians
   const StepConst sc = [&] {
     double tr, ta, itr, ita;

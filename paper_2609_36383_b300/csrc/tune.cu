@@ -30,19 +30,26 @@ extern "C" int pic_tune_sort(pic_ctx *ctx, double tol, int steps, const int *can
   const long long st_l = ctx->launches, st_ml = ctx->map_launches, st_p = ctx->pushes,
                   st_i = ctx->inner_iters, st_pc = ctx->pieces, st_r = ctx->refined;
   const double st_ms = ctx->map_ms;
-  // exact checkpoint of the accepted state (the device arrays themselves)
-  uint64_t nbytes = 0;
+  // exact snapshot of the accepted state (the device arrays themselves, in
+  // device memory)
+  struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() {
+      if (p) cudaFree(p);
+    }
+  } snap;
   int e;
-  if ((e = pic_checkpoint_bytes(ctx, &nbytes))) return e;
-  std::vector<unsigned char> image(nbytes);
-  if ((e = pic_checkpoint_save(ctx, image.data(), nbytes))) return e;
+  CK(cudaMalloc(&snap.p, state_snapshot_bytes(ctx)));
+  if ((e = state_snapshot(ctx, snap.p))) return e;
   const int sort0 = ctx->opt.sort_every;
-  // every candidate starts from the checkpoint, sorted by cell when it sorts
+  const long long steps0 = ctx->steps_done;
+  const double E0 = ctx->E0;
+  const int64_t np0 = ctx->np;
+  // every candidate starts from the snapshot, sorted by cell when it sorts
   // at all (as pic_start leaves the particles)
   auto restore = [&](int sort_every, bool sort_now) -> int {
-    int r = pic_checkpoint_load(ctx, image.data(), nbytes);
+    int r = state_restore(ctx, snap.p, np0, steps0, sort_every, E0);
     if (r) return r;
-    ctx->opt.sort_every = sort_every;
     return sort_now && sort_every > 0 ? particles_sort(ctx) : PIC_OK;
   };
   cudaEvent_t ea, eb;
