@@ -236,3 +236,36 @@ def test_state_after_autograd_gradient_matches_central_differences():
     print(f"autograd <grad, d> {lhs:.10e}, central difference {fd:.10e}, "
           f"|diff| / gross {abs(lhs - fd) / gross:.2e}")
     assert abs(lhs - fd) <= 1e-5 * gross
+
+
+def test_step_vjp_with_device_buffers_matches_host_buffers():
+    """on_device = 1: the cotangents in and out as CUDA device pointers give
+    the host call's results (to the atomic scatters' summation order)."""
+    import ctypes as C
+    import torch
+    cfg = small_2d()
+    s = make_gpu(cfg)
+    s.start()
+    assert s.step(TOL)["status"] == 0
+    N, Ng, d = s.num_particles(), s.Ng, s.dim
+    rng = np.random.default_rng(3)
+    cx = rng.standard_normal((d, N))
+    cP = rng.standard_normal((3, N))
+    cf = {k: rng.standard_normal(v.shape) for k, v in s.fields().items() if k != "J"}
+    ref = s.step_vjp(TOL, cx, cP, cf)
+    dev = torch.device("cuda")
+    t_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+            for a in (cx, cP, s._pack_fields(cf))]
+    t_out = [torch.zeros(d * N, dtype=torch.float64, device=dev),
+             torch.zeros(3 * N, dtype=torch.float64, device=dev),
+             torch.zeros(9 * Ng, dtype=torch.float64, device=dev)]
+    its = C.c_int(0)
+    torch.cuda.synchronize()
+    rc = pic.lib().pic_step_vjp(s.handle, TOL, *[C.c_void_p(t.data_ptr()) for t in t_in],
+                                *[C.c_void_p(t.data_ptr()) for t in t_out], C.byref(its), 1)
+    assert rc == 0
+    torch.cuda.synchronize()
+    got = [t.cpu().numpy() for t in t_out]
+    want = [ref["x"].ravel(), ref["P"].ravel(), s._pack_fields(ref["fields"])]
+    for g, w in zip(got, want):
+        assert np.abs(g - w).max() <= 1e-10 * np.abs(w).max()
