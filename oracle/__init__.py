@@ -94,6 +94,7 @@ def lib():
         L.orc_get_particles.argtypes = [C.c_void_p, _D, _D, _D, _I]
         L.orc_get_fields.argtypes = [C.c_void_p, _D, _D, _D, _D, _D, _D]
         L.orc_set_fields.argtypes = [C.c_void_p, _D, _D, _D, _D, _D, _D]
+        L.orc_knot_jumps.argtypes = [C.c_void_p, C.c_double, _D, _D]
         L.orc_set_state.argtypes = [C.c_void_p, C.c_long, C.POINTER(C.c_int), _D, _D, _D, _D, _D,
                                     _D, _D, _D, _D]
         L.orc_S2.restype = C.c_double
@@ -297,6 +298,12 @@ class Oracle:
     def set_fields(self, phi=None, psi=None, A=None, U=None, rho=None, J=None):
         vals = [None if v is None else _f64(v) for v in (phi, psi, A, U, rho, J)]
         lib().orc_set_fields(self._h, *[_p(v) for v in vals])
+
+    def knot_jumps(self, eps=1e-8):
+        """(E_shape jump, grad A jump) maxima over the interpolant's knots (Sec. 5.3)."""
+        Ej, Gj = C.c_double(0.0), C.c_double(0.0)
+        lib().orc_knot_jumps(self._h, float(eps), C.byref(Ej), C.byref(Gj))
+        return Ej.value, Gj.value
 
     def set_state(self, x, P, w, species, fields):
         """A full accepted state (canonical momenta, every mesh array); the

@@ -773,6 +773,93 @@ int orc_set_fields(void *h, const double *phi, const double *psi, const double *
   return ORC_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* knot-jump regularity diagnostic, Sec. 5.3                           */
+/* ------------------------------------------------------------------ */
+/* The field interpolants F_h(x) = sum_g F_g S(x - x_g) with the particle
+   shape S of degree o->p.order, at the point u (node units, unwrapped):
+   grad phi_h, U_h and grad A_h (columns per active dimension, physical
+   units), from the B-spline formula on every node of a window of 6 nodes
+   per active dimension around u (the support is 2 or 3 nodes wide). */
+static void field_interp_at(const orc *o, const double u[3], double gphi[3], double Uh[3],
+                            double gA[3][3]) {
+  const int d = o->p.dim;
+  const size_t Ng = (size_t)o->Ng;
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int l = 0; l < 3; l++) {
+    gphi[l] = Uh[l] = 0.0;
+    for (int j = 0; j < 3; j++) gA[l][j] = 0.0;
+    if (l < d) {
+      lo[l] = (int)floor(u[l]) - 2;
+      hi[l] = lo[l] + 5;
+    }
+  }
+  for (int m2 = lo[2]; m2 <= hi[2]; m2++)
+    for (int m1 = lo[1]; m1 <= hi[1]; m1++)
+      for (int m0 = lo[0]; m0 <= hi[0]; m0++) {
+        const int m[3] = {m0, m1, m2};
+        double S[3] = {1.0, 1.0, 1.0}, dS[3] = {0.0, 0.0, 0.0};
+        size_t g = 0, stride = 1;
+        for (int l = 0; l < d; l++) {
+          const double xi = u[l] - m[l];
+          S[l] = shp(o, xi);
+          dS[l] = dshp(o, xi) / o->dx[l];
+          const int n = o->p.n[l];
+          g += stride * (size_t)(((m[l] % n) + n) % n);
+          stride *= (size_t)n;
+        }
+        const double W = S[0] * S[1] * S[2];
+        for (int c = 0; c < 3; c++) Uh[c] += o->U[c * Ng + g] * W;
+        for (int l = 0; l < d; l++) {
+          double Wd = dS[l];
+          for (int q = 0; q < d; q++)
+            if (q != l) Wd *= S[q];
+          gphi[l] += o->phi[g] * Wd;
+          for (int c = 0; c < 3; c++) gA[c][l] += o->A[c * Ng + g] * Wd;
+        }
+      }
+}
+
+/* For every active axis a and every node, the knot of the interpolant that
+   follows the node along a (half a cell on for S_2, the node itself for
+   S_1) is probed at +-eps (node units) along a.  The other coordinates sit
+   half a cell away from their own knots (on the node for S_2, at the cell
+   centre for S_1), where the interpolant is smooth in them.  The jumps are
+   |E(+) - E(-)| of E_shape = -grad phi_h - U_h (Euclidean norm) and
+   |G(+) - G(-)| of G = grad A_h (Frobenius norm); returns their maxima. */
+int orc_knot_jumps(void *h, double eps, double *E_jump, double *G_jump) {
+  orc *o = (orc *)h;
+  const int d = o->p.dim;
+  double Emax = 0.0, Gmax = 0.0;
+  for (int a = 0; a < d; a++)
+    for (long g = 0; g < o->Ng; g++) {
+      long r = g;
+      double u[3] = {0.0, 0.0, 0.0};
+      const double side_off = o->p.order == 1 ? 0.5 : 0.0;  // transverse: off the knots
+      for (int l = 0; l < d; l++) {
+        u[l] = (double)(r % o->p.n[l]) + (l == a ? 0.0 : side_off);
+        r /= o->p.n[l];
+      }
+      double E[2][3], G[2][3][3];
+      for (int side = 0; side < 2; side++) {
+        double up[3] = {u[0], u[1], u[2]}, gphi[3], Uh[3];
+        up[a] += knot_off(o) + (side ? eps : -eps);
+        field_interp_at(o, up, gphi, Uh, G[side]);
+        for (int c = 0; c < 3; c++) E[side][c] = -(c < d ? gphi[c] : 0.0) - Uh[c];
+      }
+      double e2 = 0.0, g2 = 0.0;
+      for (int c = 0; c < 3; c++) {
+        e2 += (E[1][c] - E[0][c]) * (E[1][c] - E[0][c]);
+        for (int l = 0; l < d; l++) g2 += (G[1][c][l] - G[0][c][l]) * (G[1][c][l] - G[0][c][l]);
+      }
+      if (sqrt(e2) > Emax) Emax = sqrt(e2);
+      if (sqrt(g2) > Gmax) Gmax = sqrt(g2);
+    }
+  *E_jump = Emax;
+  *G_jump = Gmax;
+  return ORC_OK;
+}
+
 int orc_set_state(void *h, long np, const int *species, const double *x, const double *P,
                   const double *w, const double *phi, const double *psi, const double *A,
                   const double *U, const double *rho, const double *J) {

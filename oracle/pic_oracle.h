@@ -81,6 +81,14 @@ int orc_get_fields(void *h, double *phi, double *psi, double *A, double *U,
 int orc_set_fields(void *h, const double *phi, const double *psi, const double *A,
                    const double *U, const double *rho, const double *J);
 
+/* The knot-jump regularity diagnostic of Sec. 5.3: the maxima, over every
+   knot of the field interpolant (the particle shape's knots) along every
+   active axis, with the other coordinates half a cell from their knots
+   (on nodes for S_2, at cell centres for S_1), of the two-sided
+   differences at +-eps node units of E_shape = -grad phi_h - U_h
+   (Euclidean norm) and of grad A_h (Frobenius norm). */
+int orc_knot_jumps(void *h, double eps, double *E_jump, double *G_jump);
+
 /* A full accepted state, as after pic_start or a step (test support, no
    arithmetic): particles with canonical momenta and every mesh array; the
    context is then started, so orc_step continues from it. */

@@ -166,3 +166,93 @@ def test_refinement_inactive_changes_nothing(orc):
     xa, Pa, _, _ = a.particles()
     xb, Pb, _, _ = b.particles()
     assert np.array_equal(xa, xb) and np.array_equal(Pa, Pb)
+
+
+# ---- knot-jump regularity diagnostic (Sec. 5.3) ---------------------------
+# The interpolant F_h = sum_g F_g S_r(x - x_g) has knots where S_r changes
+# polynomial piece: the nodes for r = 1, the cell midpoints for r = 2.  With
+# the probe at +-eps node units about a knot, closed forms follow from the
+# piecewise structure:
+#  * r = 1: F_h is linear between nodes, so d F_h / dx jumps at node i by the
+#    second difference (F_{i+1} - 2 F_i + F_{i-1}) / dx;
+#  * r = 2: d F_h / dx is continuous and piecewise linear, with slope
+#    D_i = (F_{i+1} - 2 F_i + F_{i-1}) / dx^2 on the cell of node i, so the
+#    two-sided difference across the knot between nodes i and i + 1 is
+#    eps dx (D_i + D_{i+1});
+#  * a separable field F_{ij} = f_i g_j probed along x on a line y = y* half a
+#    cell from the y-knots (y_j for r = 2, y_{j+1/2} for r = 1) has
+#    E = -(f_h'(x) g_h(y*), f_h(x) g_h'(y*)): the x-component jumps by the
+#    slope jump of f times g_h(y*), and the y-component changes by
+#    f_h(x+) - f_h(x-) = eps (f_{i+1} - f_{i-1}) (r = 1) or
+#    2 eps (f_{i+1} - f_i) (r = 2, to O(eps^2)) times g_h'(y*), with
+#    g_h(y_{j+1/2}) = (g_j + g_{j+1}) / 2 and g_h' = (g_{j+1} - g_j) / dx
+#    (r = 1), g_h(y_j) = (g_{j-1} + 6 g_j + g_{j+1}) / 8 and
+#    g_h'(y_j) = (g_{j+1} - g_{j-1}) / (2 dx) (r = 2, from S_2 and S_2' at
+#    0 and +-1).
+
+def _second_diff(f):
+    return np.roll(f, -1) - 2 * f + np.roll(f, 1)
+
+
+def _jumps_1d(o, phi=None, A=None, eps=1e-8):
+    Ng = o.Ng
+    z1, z3 = np.zeros(Ng), np.zeros(3 * Ng)
+    o.set_state(np.zeros((o.dim, 0)), np.zeros((3, 0)), np.zeros(0), np.zeros(0, np.int32),
+                dict(phi=z1 if phi is None else phi, psi=z1, A=z3 if A is None else A, U=z3,
+                     rho=z1, J=z3))
+    return o.knot_jumps(eps)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_knot_jump_closed_forms_in_1d(orc, order):
+    n, L, eps = 32, 4 * math.pi, 1e-8
+    dx = L / n
+    o = orc.Oracle(1, [n], [L], [0.0], [(-1.0, 1.0)], dt=0.1, order=order)
+    rng = np.random.default_rng(40 + order)
+    phi = rng.standard_normal(n)
+    A = rng.standard_normal(3 * n)
+    Ej, Gj = _jumps_1d(o, phi=phi)
+    Ej0, Gj_A = _jumps_1d(o, A=A)
+    assert Gj == 0.0 and Ej0 == 0.0
+    Ac = A.reshape(3, n)
+    if order == 1:
+        want_E = np.abs(_second_diff(phi)).max() / dx
+        want_G = np.sqrt((_second_diff(Ac.T.T) ** 2).sum(axis=0)).max() / dx
+        assert Ej == pytest.approx(want_E, rel=1e-12)
+        assert Gj_A == pytest.approx(want_G, rel=1e-12)
+    else:
+        D = _second_diff(phi) / dx ** 2
+        want_E = (eps * dx * np.abs(D + np.roll(D, -1))).max()
+        DA = np.stack([_second_diff(a) for a in Ac]) / dx ** 2
+        want_G = (eps * dx * np.sqrt(((DA + np.roll(DA, -1, axis=1)) ** 2).sum(axis=0))).max()
+        assert Ej == pytest.approx(want_E, rel=1e-6)
+        assert Gj_A == pytest.approx(want_G, rel=1e-6)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_knot_jump_separable_field_in_2d(orc, order):
+    n, L, eps = 16, 2 * math.pi, 1e-8
+    dx = L / n
+    o = orc.Oracle(2, [n, n], [L, L], [-math.pi, -math.pi], [(-1.0, 1.0)], dt=0.1, order=order)
+    rng = np.random.default_rng(7 + order)
+    f, g = rng.standard_normal(n), rng.standard_normal(n)
+    phi = np.outer(g, f).ravel()  # phi[i + n j] = f_i g_j (x fastest)
+
+    def along(v, w):
+        """max jump probing along the axis of v, the transverse factor w."""
+        if order == 1:
+            a = _second_diff(v) / dx                      # slope jump at node i
+            dv = eps * (np.roll(v, -1) - np.roll(v, 1))   # v_h(x+) - v_h(x-)
+            wh = (w + np.roll(w, -1)) / 2
+            wp = (np.roll(w, -1) - w) / dx
+        else:
+            D = _second_diff(v) / dx ** 2
+            a = eps * dx * (D + np.roll(D, -1))           # across the knot i + 1/2
+            dv = 2 * eps * (np.roll(v, -1) - v)
+            wh = (np.roll(w, 1) + 6 * w + np.roll(w, -1)) / 8
+            wp = (np.roll(w, -1) - np.roll(w, 1)) / (2 * dx)
+        return np.sqrt(np.outer(a, wh) ** 2 + np.outer(dv, wp) ** 2).max()
+
+    Ej, _ = _jumps_1d(o, phi=phi)
+    want = max(along(f, g), along(g, f))
+    assert Ej == pytest.approx(want, rel=1e-12 if order == 1 else 1e-6)
