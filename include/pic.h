@@ -375,6 +375,20 @@ int pic_checkpoint_inspect(const void *image, uint64_t bytes, pic_checkpoint_hea
    state is set again. */
 int pic_checkpoint_load(pic_ctx *ctx, const void *image, uint64_t bytes);
 
+/* The knot-jump regularity diagnostic of Sec. 5.3 on the accepted fields.
+   The field interpolants F_h = sum_g F_g S_r(x - x_g) use the context's
+   particle shape (degree r = pic_options.order).  They are probed at every
+   knot of S_r (the nodes for r = 1, the cell midpoints for r = 2) along
+   every active axis, at +-eps node units along the axis (the paper uses
+   eps = 1e-8).  The other coordinates sit half a cell from their own knots:
+   on the node for r = 2, at the cell centre for r = 1.  *E_jump receives
+   the largest |E(+) - E(-)| of E_shape = -grad phi_h - U_h (Euclidean
+   norm), *G_jump the largest |G(+) - G(-)| of G = grad A_h (Frobenius
+   norm, columns per active dimension).  O(1) jumps mark the discontinuous
+   first derivatives of r = 1, O(eps) the continuous ones of r = 2.
+   PIC_EARG unless 0 < eps < 1/4; PIC_ESTATE before pic_start. */
+int pic_knot_jumps(pic_ctx *ctx, double eps, double *E_jump, double *G_jump);
+
 /* Counters of the work this context has done (library profiling support;
    the paper has no counterpart).  map_ms is the device time of the particle
    map kernel (inner solves + deposit) measured with CUDA events recorded on

@@ -30,7 +30,7 @@ EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_pote
            "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_checkpoint_bytes",
            "pic_checkpoint_save", "pic_checkpoint_inspect", "pic_checkpoint_load",
            "pic_get_stats", "pic_reset_stats",
-           "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_last_error", "pic_free",
+           "pic_fma_throughput", "pic_kinetic_energy_noalloc", "pic_knot_jumps", "pic_last_error", "pic_free",
            "pic_batch_init", "pic_batch_set_instance", "pic_batch_start", "pic_batch_step",
            "pic_batch_num_particles", "pic_batch_get_particles", "pic_batch_get_potentials",
            "pic_batch_get_stats", "pic_batch_reset_stats", "pic_batch_last_error", "pic_batch_free")
@@ -144,6 +144,7 @@ def lib():
         L.pic_checkpoint_inspect.argtypes = [_VP, C.c_uint64, C.POINTER(CheckpointHeader),
                                              C.c_char_p, C.c_int]
         L.pic_checkpoint_load.argtypes = [_VP, _VP, C.c_uint64]
+        L.pic_knot_jumps.argtypes = [_VP, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.pic_get_stats.argtypes = [_VP, C.POINTER(Stats)]
         L.pic_reset_stats.argtypes = [_VP]
         L.pic_fma_throughput.argtypes = [C.c_int, C.POINTER(C.c_double)]
@@ -497,6 +498,13 @@ class Simulation:
     def load_checkpoint(self, path):
         with open(path, "rb") as f:
             self.restore(f.read())
+
+    def knot_jumps(self, eps=1e-8):
+        """(E_shape jump, grad A jump): the knot-jump regularity diagnostic of
+        Sec. 5.3 on the accepted fields (pic_knot_jumps)."""
+        Ej, Gj = C.c_double(0.0), C.c_double(0.0)
+        self._check(lib().pic_knot_jumps(self._h, float(eps), C.byref(Ej), C.byref(Gj)))
+        return Ej.value, Gj.value
 
     def stats(self) -> dict:
         st = Stats()
