@@ -40,3 +40,4 @@ __device__ __forceinline__ CSum csum_warp(CSum a) {
   }
   return a;
 }
+

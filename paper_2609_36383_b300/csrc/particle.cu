@@ -8,6 +8,9 @@
 
 namespace {
 
+// second level of the particle sums (k_psum_level2)
+constexpr int kPsumBlocks = 128, kPsumThreads = 256;
+
 // ---- simple per-particle kernels -------------------------------------------
 template <int D, typename T>
 __global__ void k_load(int64_t n, int64_t cap, const double *__restrict__ x,
@@ -138,8 +141,9 @@ __global__ void k_commit(int64_t np, int64_t cap, int32_t *cell, T *off, T *P,
 }
 
 // kinetic energy m kappa^2 (gamma - 1) = |p|^2 / (m (gamma + 1)), p = P - q A_h(x)
-// (Eq. Kkin-nondim): per particle in the particle real type, summed in FP64
-// with compensation (block (sum, error) pairs merged on the host)
+// (Eq. Kkin-nondim): per particle in the particle real type, summed in FP64:
+// plainly within a warp, with compensation across warps and blocks (block
+// (sum, error) pairs merged on the host)
 template <int D, typename T>
 __global__ void __launch_bounds__(kPT)
 k_kinetic(PView<T> pv, const T *__restrict__ AT, PGeom pg, KConst<T> kc, double *psum) {
@@ -165,15 +169,58 @@ k_kinetic(PView<T> pv, const T *__restrict__ AT, PGeom pg, KConst<T> kc, double 
     T gam = sqrt(T(1) + p2 * im * im / (kc.kappa * kc.kappa));
     k = p2 * im / (gam + T(1));
   }
-  const CSum kw = csum_warp(CSum{widen(k), 0.0});
-  __shared__ CSum sh[kPT / 32];
+  // a warp's 32 positive terms summed plainly (a 5-level tree: a few ulps of
+  // the warp's sum, errors independent from warp to warp, and 5 FP64 adds a
+  // lane instead of 5 TwoSums); warps and blocks merged with compensation
+  double kw = widen(k);
+  for (int o = 16; o > 0; o >>= 1) kw += __shfl_down_sync(0xffffffffu, kw, o);
+  __shared__ double sh[kPT / 32];
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = kw;
   __syncthreads();
   if (threadIdx.x == 0) {
     CSum t = csum_zero();
-    for (int w = 0; w < kPT / 32; w++) t = csum_merge(t, sh[w]);
+    for (int w = 0; w < kPT / 32; w++) csum_add(t, sh[w]);
     psum[2 * blockIdx.x] = t.s;
     psum[2 * blockIdx.x + 1] = t.c;
+  }
+}
+
+// Second level of the particle sums, on the device: the nb block partials
+// at in[2b], in[2b + 1] (two plain quantities, pairs = 0, or one (sum,
+// error) pair, pairs = 1) merged with compensation by kPsumBlocks blocks,
+// each over a contiguous range, into out[4k .. 4k + 3] = (sum, error) of
+// the first and of the second quantity.  Fixed order, so reproducible; the
+// host then merges kPsumBlocks entries instead of nb.
+__global__ void __launch_bounds__(kPsumThreads)
+k_psum_level2(const double *__restrict__ in, int64_t nb, int pairs, double *__restrict__ out) {
+  const int64_t lo = nb * blockIdx.x / kPsumBlocks, hi = nb * (blockIdx.x + 1) / kPsumBlocks;
+  CSum a = csum_zero(), b = csum_zero();
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kPsumThreads) {
+    if (pairs) {
+      a = csum_merge(a, CSum{in[2 * i], in[2 * i + 1]});
+    } else {
+      csum_add(a, in[2 * i]);
+      csum_add(b, in[2 * i + 1]);
+    }
+  }
+  a = csum_warp(a);
+  b = csum_warp(b);
+  __shared__ CSum sa[kPsumThreads / 32], sb[kPsumThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    sa[threadIdx.x >> 5] = a;
+    sb[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    CSum ta = csum_zero(), tb = csum_zero();
+    for (int w = 0; w < kPsumThreads / 32; w++) {
+      ta = csum_merge(ta, sa[w]);
+      tb = csum_merge(tb, sb[w]);
+    }
+    out[4 * blockIdx.x] = ta.s;
+    out[4 * blockIdx.x + 1] = ta.c;
+    out[4 * blockIdx.x + 2] = tb.s;
+    out[4 * blockIdx.x + 3] = tb.c;
   }
 }
 
@@ -325,10 +372,10 @@ int particles_alloc(pic_ctx *ctx, int64_t n) {
   CK(cudaMalloc((void **)&ctx->tmp_i, sizeof(int32_t) * cap));
   CK(cudaMalloc((void **)&ctx->keys, sizeof(int32_t) * cap));
   CK(cudaMalloc((void **)&ctx->tmp_l, sizeof(int64_t) * cap));
-  CK(cudaMalloc((void **)&ctx->psum, sizeof(double) * 4 * nb + 64));
+  CK(cudaMalloc((void **)&ctx->psum, sizeof(double) * (4 * nb + 4 * kPsumBlocks) + 64));
   if (ctx->psum_host) cudaFreeHost(ctx->psum_host);
   ctx->psum_host = nullptr;
-  CK(cudaMallocHost((void **)&ctx->psum_host, sizeof(double) * 4 * nb + 64));
+  CK(cudaMallocHost((void **)&ctx->psum_host, sizeof(double) * (4 * nb + 4 * kPsumBlocks) + 64));
   CK(cudaMemsetAsync(ctx->cell, 0, sizeof(int32_t) * 3 * cap, ctx->st));
   CK(cudaMemsetAsync(ctx->off, 0, R * 3 * cap, ctx->st));
   ctx->cap = cap;
@@ -435,9 +482,13 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
       int e = det_deposit(ctx, ctx->Jorb, sc_in);
       if (e) return e;
     }
-    if (final_pass)  // block partials of the work and chain-rule sums
-      CK(cudaMemcpyAsync(ctx->psum_host, ctx->psum, sizeof(double) * 2 * nb,
-                         cudaMemcpyDeviceToHost, ctx->st));
+    if (final_pass) {  // the work and chain-rule sums: block partials merged on the device
+      k_psum_level2<<<kPsumBlocks, kPsumThreads, 0, ctx->st>>>(ctx->psum, nb, 0,
+                                                              ctx->psum + 2 * (size_t)nb);
+      KCHECK();
+      CK(cudaMemcpyAsync(ctx->psum_host, ctx->psum + 2 * (size_t)nb,
+                         sizeof(double) * 4 * kPsumBlocks, cudaMemcpyDeviceToHost, ctx->st));
+    }
   }
   CK(cudaMemcpyAsync(ctx->cnt_host, ctx->cnt_dev, sizeof(EvalCounters), cudaMemcpyDeviceToHost,
                      ctx->st));
@@ -452,11 +503,11 @@ int particles_map_finish(pic_ctx *ctx, double *work_sum, double *chain_sum, Eval
     ctx->map_ms += ms;
     ctx->map_launches++;
     if (ctx->map_final) {  // fixed order, compensated: reproducible diagnostics
-      int nb = nblk(ctx->np);
+      const double *ps = ctx->psum_host;  // kPsumBlocks (sum, error) pairs of each
       CSum cw = csum_zero(), cc = csum_zero();
-      for (int b = 0; b < nb; b++) {
-        csum_add(cw, ctx->psum_host[2 * b]);
-        csum_add(cc, ctx->psum_host[2 * b + 1]);
+      for (int k = 0; k < kPsumBlocks; k++) {
+        cw = csum_merge(cw, CSum{ps[4 * k], ps[4 * k + 1]});
+        cc = csum_merge(cc, CSum{ps[4 * k + 2], ps[4 * k + 3]});
       }
       work = csum_value(cw);
       chain = csum_value(cc);
@@ -490,12 +541,15 @@ int particles_kinetic(pic_ctx *ctx, double *K) {
   PIC_DISPATCH(ctx, (k_kinetic<DD, RT><<<nb, kPT, 0, ctx->st>>>(
                          pview<RT>(ctx), A_typed<RT>(ctx), pg, kconst<RT>(sc, pg), ctx->psum)));
   KCHECK();
-  CK(cudaMemcpyAsync(ctx->psum_host, ctx->psum, sizeof(double) * 2 * nb,
-                     cudaMemcpyDeviceToHost, ctx->st));
+  k_psum_level2<<<kPsumBlocks, kPsumThreads, 0, ctx->st>>>(ctx->psum, nb, 1,
+                                                          ctx->psum + 2 * (size_t)nb);
+  KCHECK();
+  CK(cudaMemcpyAsync(ctx->psum_host, ctx->psum + 2 * (size_t)nb,
+                     sizeof(double) * 4 * kPsumBlocks, cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  const double *ps = ctx->psum_host;
   CSum k = csum_zero();
-  for (int b = 0; b < nb; b++)  // fixed order
-    k = csum_merge(k, CSum{ctx->psum_host[2 * b], ctx->psum_host[2 * b + 1]});
+  for (int b = 0; b < kPsumBlocks; b++) k = csum_merge(k, CSum{ps[4 * b], ps[4 * b + 1]});
   *K = csum_value(k);
   return PIC_OK;
 }
