@@ -599,6 +599,34 @@ def oracle_one_map_evaluation():
                        f"({npart} particles)")
 
 
+def oracle_two_stream_run(seconds_budget=30.0):
+    """The FP64 oracle on the whole 1D two-stream run (64 nodes, 4,096
+    particles, 200 steps at dt = 0.1, tol 1e-12), stopped early if it passes
+    the time budget; all host cores."""
+    import oracle
+    import pic_inputs
+    oracle.build()
+    cfg = pic_inputs.two_stream_1d(nx=64, ppc_beam=32)
+    o = oracle.Oracle(cfg["dim"], cfg["n"], cfg["L"], cfg["x0"], cfg["species"], dt=cfg["dt"],
+                      rho_bg=cfg["rho_bg"])
+    o.set_particles(cfg["x"], cfg["u"], cfg["w"], cfg["sp"])
+    o.set_potentials(cfg["A"], cfg["U"])
+    o.start()
+    npart = cfg["w"].shape[0]
+    total = 200
+    pushes, secs, n = 0, 0.0, 0
+    while n < total and secs < seconds_budget:
+        t0 = time.perf_counter()
+        r = o.step(cfg["tol"])
+        secs += time.perf_counter() - t0
+        pushes += npart * r["map_evals"]
+        n += 1
+    return dict(value=pushes / secs, unit=UNIT, cores=int(os.environ.get("OMP_NUM_THREADS",
+                                                                        os.cpu_count())),
+                kind="oracle", seconds=secs, steps=n,
+                sample=f"two_stream_1d (64 nodes, {npart} particles): {n} of {total} steps")
+
+
 def _oracle_subprocess(flag, threads):
     env = dict(os.environ)
     env["OMP_NUM_THREADS"] = str(threads)
@@ -619,6 +647,16 @@ def cpu_baseline_subprocess(args):
     out = _oracle_subprocess("--cpu-sample", int(os.environ.get("OMP_NUM_THREADS",
                                                                 os.cpu_count())))
     out["one_core"] = _oracle_subprocess("--cpu-sample-one", 1)
+    out["two_stream_1d"] = _oracle_subprocess("--cpu-sample-1d", int(
+        os.environ.get("OMP_NUM_THREADS", os.cpu_count())))
+    if out.get("value"):
+        n_large, evals = 512 * 512 * 256, 5
+        out["large_extrapolated"] = {
+            "value": out["value"], "unit": UNIT, "kind": "extrapolated",
+            "seconds_per_step": n_large * evals / out["value"],
+            "note": "the 512x512, 67,108,864-particle case is too large for the oracle: its "
+                    "per-push cost is taken from the 128x128 sample (the particle map's cost "
+                    "per push does not grow with the mesh), 5 map evaluations per step"}
     return out
 
 
@@ -663,7 +701,11 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true", help="profiling run without the e2e arm")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sample-one", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-sample-1d", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_sample_1d:
+        print(json.dumps(oracle_two_stream_run()), flush=True)
+        return
     if args.cpu_sample:
         print(json.dumps(oracle_sample()), flush=True)
         return
