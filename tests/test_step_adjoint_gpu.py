@@ -269,3 +269,37 @@ def test_step_vjp_with_device_buffers_matches_host_buffers():
     want = [ref["x"].ravel(), ref["P"].ravel(), s._pack_fields(ref["fields"])]
     for g, w in zip(got, want):
         assert np.abs(g - w).max() <= 1e-10 * np.abs(w).max()
+
+
+@pytest.mark.parametrize("project", [1, 0])
+def test_vacuum_step_adjoint_is_the_transpose_of_the_field_step(project):
+    """No particles: the step is the CN field update alone, linear in the
+    state, so <ybar, step(dS)> = <step^T ybar, dS> to rounding for any dS
+    (checked through the linear map itself, step(S + dS) - step(S)), with
+    and without the Nyquist projector."""
+    cfg = small_2d()
+    n, Ng = cfg["n"], int(np.prod(cfg["n"]))
+    rng = np.random.default_rng(30 + project)
+    s = pic.Simulation(2, n, cfg["L"], cfg["x0"], cfg["species"], cfg["dt"],
+                       project_nyquist=project)
+    empty = (np.zeros((2, 0)), np.zeros((3, 0)), np.zeros(0), np.zeros(0, np.int32))
+    f0 = {k: rng.standard_normal(m * Ng) for k, m in
+          (("phi", 1), ("psi", 1), ("A", 3), ("U", 3), ("rho", 1))}
+    f0["J"] = np.zeros(3 * Ng)
+    d = {k: rng.standard_normal(v.shape) for k, v in f0.items() if k != "J"}
+    yb = {k: rng.standard_normal(v.shape) for k, v in f0.items() if k != "J"}
+
+    def step_from(f):
+        s.set_state(*empty, f, 1.0)
+        assert s.step(1e-12)["status"] == 0
+        return s.fields()
+
+    base = step_from(f0)
+    moved = step_from({**f0, **{k: f0[k] + d[k] for k in d}})
+    lhs = sum(np.sum(yb[k] * (moved[k] - base[k])) for k in yb)
+    s.set_state(*empty, f0, 1.0)
+    g = s.step_vjp(1e-12, fbar=yb)["fields"]
+    rhs = sum(np.sum(g[k] * d[k]) for k in d)
+    gross = sum(np.sum(np.abs(yb[k] * (moved[k] - base[k]))) for k in yb)
+    print(f"project {project}: <ybar, step dS> {lhs:.14e}, <step^T ybar, dS> {rhs:.14e}")
+    assert abs(lhs - rhs) <= 1e-12 * gross
