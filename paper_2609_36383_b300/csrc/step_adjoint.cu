@@ -643,15 +643,10 @@ extern "C" int pic_step_vjp(pic_ctx *ctx, double tol, const double *xbar1, const
   } snap;
   CK(cudaMalloc(&snap.p, state_snapshot_bytes(ctx)));
   if ((e = state_snapshot(ctx, snap.p))) return e;
-  const long long steps0 = ctx->steps_done;
-  const int sort0 = ctx->opt.sort_every;
-  const double E00 = ctx->E0;
-  pic_report rep;
-  const int st_step = pic_step(ctx, tol, &rep);
-  if (st_step != PIC_OK) return st_step;  // a failed step leaves S^n in place
   const int64_t np = ctx->np;
   const size_t cap = (size_t)ctx->cap;
-  // scratch (after the step: the load below keeps the particle capacity)
+  // scratch, before the step, so that nothing after the step can fail
+  // before the snapshot is restored but a copy (a step keeps np and cap)
   const size_t n_mesh = (size_t)(d + 6) * Ng  // Fbar
                         + 9 * (size_t)Ng      // next-state cotangents (real)
                         + 9 * (size_t)Ng      // current-state cotangents (real)
@@ -680,6 +675,12 @@ extern "C" int pic_step_vjp(pic_ctx *ctx, double tol, const double *xbar1, const
   double *jvs = vbs + 3 * cap, *jps = jvs + 9 * cap, *mus = jps + 9 * cap, *xb1s = mus + 3 * cap,
          *Pb1s = xb1s + 3 * cap, *xb0s = Pb1s + 3 * cap, *Pb0s = xb0s + 3 * cap,
          *ptmp = Pb0s + 3 * cap;  // 3 x np rows in load order
+  const long long steps0 = ctx->steps_done;
+  const int sort0 = ctx->opt.sort_every;
+  const double E00 = ctx->E0;
+  pic_report rep;
+  const int st_step = pic_step(ctx, tol, &rep);
+  if (st_step != PIC_OK) return st_step;  // a failed step leaves S^n in place
   CK(cudaMemcpyAsync(jstar, ctx->J_acc, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   if ((e = state_restore(ctx, snap.p, np, steps0, sort0, E00))) return e;
