@@ -106,3 +106,26 @@ def test_deterministic_deposit_rejected_where_unsupported_without_touching_the_g
     npart = (ctypes.c_int64 * 2)(10, 10)
     assert P.lib().pic_batch_init(ctypes.byref(h), 2, n, L, None, npart, sp, 1, 0.1,
                                   ctypes.byref(o)) == P.PIC_EARG
+
+
+def test_new_entry_points_refuse_a_null_context_without_touching_the_gpu(libpic):
+    """The checkpoint, step-adjoint and regularity calls check their context
+    and arguments before any CUDA call: PIC_EARG (-1) for a null context or
+    a null output."""
+    import paper_2609_36383_b300 as P
+    L = P.lib()
+    nb = ctypes.c_uint64(0)
+    assert L.pic_checkpoint_bytes(None, ctypes.byref(nb)) == P.PIC_EARG
+    buf = ctypes.create_string_buffer(512)
+    assert L.pic_checkpoint_save(None, buf, 512) == P.PIC_EARG
+    assert L.pic_checkpoint_load(None, buf, 512) == P.PIC_EARG
+    its = ctypes.c_int(0)
+    assert L.pic_step_vjp(None, 1e-12, None, None, None, None, None, None,
+                          ctypes.byref(its), 0) == P.PIC_EARG
+    e, g = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    assert L.pic_knot_jumps(None, 1e-8, ctypes.byref(e), ctypes.byref(g)) == P.PIC_EARG
+    # inspect needs no context at all: a zero-length image is refused with a reason
+    why = ctypes.create_string_buffer(128)
+    h = P.CheckpointHeader()
+    assert L.pic_checkpoint_inspect(buf, 0, ctypes.byref(h), why, 128) == P.PIC_EARG
+    assert b"shorter than its header" in why.value
