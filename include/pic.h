@@ -143,7 +143,10 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species,
    momentum P = m u + q A_h(x) is formed by pic_start from the projected A,
    Sec. 4.5) or canonical momenta P (is_canonical = 1); w: N weights.
    The context must be started again (pic_start) unless the field state is
-   also restored with pic_set_state. */
+   also restored with pic_set_state.  Every species index must lie in
+   [0, nspecies): host arrays are checked before anything is copied, device
+   arrays by the loading kernel; either way an index out of range returns
+   PIC_EARG and leaves the context empty and unstarted. */
 int pic_set_particles(pic_ctx *ctx, int64_t n, const int32_t *species,
                       const double *x, const double *u_or_P, int is_canonical,
                       const double *w, int on_device);
@@ -422,18 +425,24 @@ int pic_fma_throughput(int precision, double *flops_per_s);
    allocations on their hot path.  It computes the same sum that pic_start
    and pic_step report as K, but needs no context.
    Arguments: grid, species (1..4) and kappa as for pic_init; n particles
-   with DEVICE arrays sp (n int32, NULL = species 0), x (dim*n absolute
+   with DEVICE arrays sp (n int32 indices in [0, nspecies), NULL = species
+   0; an index out of range returns PIC_EARG, and is never used to index
+   the species tables), x (dim*n absolute
    positions), P (3*n canonical momenta), w (n weights), A (3*Ng vector
    potential, layout as in pic_get_potentials); *K_out is a HOST double.
    The interpolation A_h uses the quadratic shape (order 2, the default).
    All work is queued on cuda_stream (NULL = legacy default stream) and the
    call returns after that stream has finished it.
-   Scratch: a fixed 128 KiB array of device memory inside the library, which
-   every GPU that loads the library holds until the process exits; at most
-   PIC_NOALLOC_MAX_PARTICLES particles, larger n returns PIC_ETOOBIG.  The
-   first call on each device looks up that array's device address
-   (cudaGetSymbolAddress) with the device current; make that first call
-   before any stream capture.  Every call shares the array, so calls whose
+   Scratch: a fixed array of 16,386 doubles (128 KiB) of device memory
+   inside the library, which every GPU that loads the library holds until
+   the process exits; at most PIC_NOALLOC_MAX_PARTICLES particles, larger n
+   returns PIC_ETOOBIG.  The first call on each device looks up that array's
+   device address (cudaGetSymbolAddress) with the device current and keeps
+   it for the process; make that first call before any stream capture.  A
+   reset of the device's primary context (cudaDeviceReset) reloads the
+   library's device code at a new address, so after one the cached address
+   is stale: do not call this function again in a process that has reset
+   the device.  Every call shares the array, so calls whose
    work overlaps on the GPU (other streams, other threads) race and must be
    serialised by the caller.  Returns PIC_EARG on invalid arguments and
    PIC_ECUDA if a launch or copy fails. */

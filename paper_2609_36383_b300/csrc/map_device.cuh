@@ -114,7 +114,8 @@ KConst<T> kconst(const StepConst &sc, const PGeom &pg) {
 // Exact widening of a deposit contribution to FP64 for the global atomics.
 // For FP32 the conversion is done with integer operations (sign, exponent
 // rebias by 1023 - 127 = 896, mantissa shift by 29) so that it does not
-// occupy the narrow FP64 pipe; FP32 subnormals (< 1.2e-38) flush to zero.
+// occupy the narrow FP64 pipe; FP32 subnormals (< 1.2e-38) flush to zero,
+// and the FP32 infinities and NaNs (exponent 255) stay infinities and NaNs.
 // Deposit of one contribution into the FP64 current J (3 Ng values); a Dual
 // contribution also deposits its tangent into the array that follows J.
 __device__ __forceinline__ void dep_add(double *J, size_t idx, size_t, double v) {
@@ -134,6 +135,9 @@ __device__ __forceinline__ double widen(float v) {
   const unsigned u = __float_as_uint(v);
   const unsigned e = (u >> 23) & 0xffu;
   if (e == 0u) return 0.0;
+  if (e == 0xffu)
+    return __hiloint2double((int)((u & 0x80000000u) | 0x7ff00000u | ((u >> 3) & 0x000fffffu)),
+                            (int)(u << 29));
   const unsigned hi = (u & 0x80000000u) | ((((u >> 3) & 0x0fffffffu)) + (896u << 20));
   const unsigned lo = u << 29;
   return __hiloint2double((int)hi, (int)lo);

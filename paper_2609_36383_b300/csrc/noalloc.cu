@@ -15,6 +15,7 @@
 // kernel forms the nearest node and offset itself.
 #include "pic_internal.cuh"
 
+#include <atomic>
 #include <cmath>
 
 namespace {
@@ -25,14 +26,18 @@ static_assert((long long)kNaMaxBlocks * kNaThreads == PIC_NOALLOC_MAX_PARTICLES,
               "PIC_NOALLOC_MAX_PARTICLES must match the scratch size");
 constexpr int kNaMaxDevices = 64;
 
-// Block partials, then one slot for the finished sum: 16385 doubles (128 KiB).
-static __device__ __align__(256) double g_noalloc_scratch[kNaMaxBlocks + 1];
+// Block partials, one slot for the finished sum, and one error word (set to
+// 1 by a thread that met a species index out of range): 16386 doubles.
+constexpr int kNaSum = kNaMaxBlocks, kNaErr = kNaMaxBlocks + 1;
+static __device__ __align__(256) double g_noalloc_scratch[kNaMaxBlocks + 2];
 
-// Device address of g_noalloc_scratch, looked up once per device.
-double *g_scratch_ptr[kNaMaxDevices] = {nullptr};
+// Device address of g_noalloc_scratch, looked up once per device.  Two
+// threads that make their first call at the same time both look it up and
+// store the same value.
+std::atomic<double *> g_scratch_ptr[kNaMaxDevices];
 
 struct NaGeom {
-  int dim, n[3], mask[3], n0, n01, Ng;
+  int dim, n[3], mask[3], n0, n01, Ng, nspecies;
   double x0[3], inv_dx[3];
   double qs[PIC_MAX_SPECIES], ms[PIC_MAX_SPECIES];
   double kappa;
@@ -74,6 +79,10 @@ k_kinetic_noalloc(int64_t n, const int32_t *__restrict__ sp, const double *__res
           for (int c = 0; c < 3; c++) Ax[c] += s * A[(size_t)c * g.Ng + gi];
         }
     int s = sp ? sp[i] : 0;
+    if (s < 0 || s >= g.nspecies) {  // never index the tables with it
+      parts[kNaErr] = 1.0;
+      s = 0;
+    }
     double q = w[i] * g.qs[s], m = w[i] * g.ms[s];
     double p2 = 0.0;
     for (int c = 0; c < 3; c++) {
@@ -94,7 +103,7 @@ k_kinetic_noalloc(int64_t n, const int32_t *__restrict__ sp, const double *__res
   }
 }
 
-// Sums the nb partials in a fixed order into parts[kNaMaxBlocks].
+// Sums the nb partials in a fixed order into parts[kNaSum].
 __global__ void k_kinetic_noalloc_final(double *parts, int nb) {
   __shared__ double sh[kNaThreads];
   double s = 0.0;
@@ -105,7 +114,7 @@ __global__ void k_kinetic_noalloc_final(double *parts, int nb) {
     if ((int)threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) parts[kNaMaxBlocks] = sh[0];
+  if (threadIdx.x == 0) parts[kNaSum] = sh[0];
 }
 
 bool na_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -144,18 +153,20 @@ extern "C" int pic_kinetic_energy_noalloc(const pic_grid *grid, const pic_specie
     if (s < nspecies && !(species[s].m > 0.0)) return PIC_EARG;
   }
   g.kappa = kappa;
+  g.nspecies = nspecies;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return PIC_ECUDA;
   // set-up, once per device, with that device current: the array's name is
   // only a host-side stand-in, so fetch the device address it refers to
-  if (!g_scratch_ptr[dev]) {
-    double *ptr = nullptr;
-    if (cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+  double *parts = g_scratch_ptr[dev].load();
+  if (!parts) {
+    if (cudaGetSymbolAddress((void **)&parts, g_noalloc_scratch) != cudaSuccess || !parts)
       return PIC_ECUDA;
-    g_scratch_ptr[dev] = ptr;
+    g_scratch_ptr[dev].store(parts);
   }
-  double *parts = g_scratch_ptr[dev];
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the error word keeps the previous call's value: clear it
+  if (cudaMemsetAsync(parts + kNaErr, 0, sizeof(double), st) != cudaSuccess) return PIC_ECUDA;
   int nb = (int)((n + kNaThreads - 1) / kNaThreads);
   if (nb > 0) {
     k_kinetic_noalloc<<<nb, kNaThreads, 0, st>>>(n, sp, x, P, w, A, g, parts);
@@ -163,9 +174,12 @@ extern "C" int pic_kinetic_energy_noalloc(const pic_grid *grid, const pic_specie
   }
   k_kinetic_noalloc_final<<<1, kNaThreads, 0, st>>>(parts, nb);
   if (cudaGetLastError() != cudaSuccess) return PIC_ECUDA;
-  if (cudaMemcpyAsync(K_out, parts + kNaMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+  double res[2];  // the sum and the error word, adjacent in the scratch
+  if (cudaMemcpyAsync(res, parts + kNaSum, sizeof res, cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)
     return PIC_ECUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PIC_ECUDA;
+  if (res[1] != 0.0) return PIC_EARG;
+  *K_out = res[0];
   return PIC_OK;
 }

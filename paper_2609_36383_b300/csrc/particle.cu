@@ -15,8 +15,9 @@ constexpr int kPsumBlocks = 128, kPsumThreads = 256;
 template <int D, typename T>
 __global__ void k_load(int64_t n, int64_t cap, const double *__restrict__ x,
                        const double *__restrict__ uP, int canonical, const double *__restrict__ w,
-                       const int32_t *__restrict__ sp, PGeom pg, int32_t *cell, T *off, T *P,
-                       double *u_in, double *wo, int32_t *spo, int64_t *id) {
+                       const int32_t *__restrict__ sp, int nspecies, PGeom pg, int32_t *cell,
+                       T *off, T *P, double *u_in, double *wo, int32_t *spo, int64_t *id,
+                       unsigned int *bad) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int l = 0; l < D; l++) {
@@ -34,7 +35,14 @@ __global__ void k_load(int64_t n, int64_t cap, const double *__restrict__ x,
     else u_in[c * cap + i] = uP[c * n + i];
   }
   wo[i] = w[i];
-  spo[i] = sp ? sp[i] : 0;
+  // a species index outside [0, nspecies) is stored as 0, so that no kernel
+  // indexes the species tables with it, and reported through *bad
+  int s = sp ? sp[i] : 0;
+  if (s < 0 || s >= nspecies) {
+    atomicOr(bad, 1u);
+    s = 0;
+  }
+  spo[i] = s;
   id[i] = i;
 }
 
@@ -403,11 +411,19 @@ int particles_load(pic_ctx *ctx, const int32_t *sp, const double *x, const doubl
     }
   }
   PGeom pg = pgeom(ctx);
+  CK(cudaMemsetAsync(ctx->cnt_dev, 0, sizeof(EvalCounters), ctx->st));
   PIC_DISPATCH(ctx, (k_load<DD, RT><<<nblk(n), kPT, 0, ctx->st>>>(
-                         n, cap, dx, du, canonical, dw, dsp, pg, ctx->cell, (RT *)ctx->off,
-                         (RT *)ctx->P, ctx->u_in, ctx->w, ctx->sp, ctx->id)));
+                         n, cap, dx, du, canonical, dw, dsp, ctx->nspecies, pg, ctx->cell,
+                         (RT *)ctx->off, (RT *)ctx->P, ctx->u_in, ctx->w, ctx->sp, ctx->id,
+                         &ctx->cnt_dev->status)));
   KCHECK();
+  CK(cudaMemcpyAsync(ctx->cnt_host, ctx->cnt_dev, sizeof(EvalCounters), cudaMemcpyDeviceToHost,
+                     ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->cnt_host->status) {
+    ctx->err = "pic_set_particles: species index out of range";
+    return PIC_EARG;
+  }
   return PIC_OK;
 }
 

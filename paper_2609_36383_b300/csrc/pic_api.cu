@@ -490,10 +490,16 @@ int pic_set_particles(pic_ctx *ctx, int64_t n, const int32_t *species, const dou
         return PIC_EARG;
       }
   graphs_clear(ctx);
+  ctx->started = 0;
   int e = particles_alloc(ctx, n);
   if (e) return e;
   ctx->np = n;
-  if ((e = particles_load(ctx, species, x, u_or_P, is_canonical, w, on_device))) return e;
+  if ((e = particles_load(ctx, species, x, u_or_P, is_canonical, w, on_device))) {
+    // a refused load leaves an empty, unstarted context
+    ctx->np = 0;
+    ctx->have_particles = 0;
+    return e;
+  }
   ctx->pending_mech = !is_canonical;
   ctx->have_particles = 1;
   ctx->started = 0;

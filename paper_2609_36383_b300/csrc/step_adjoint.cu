@@ -681,9 +681,13 @@ extern "C" int pic_step_vjp(pic_ctx *ctx, double tol, const double *xbar1, const
   pic_report rep;
   const int st_step = pic_step(ctx, tol, &rep);
   if (st_step != PIC_OK) return st_step;  // a failed step leaves S^n in place
-  CK(cudaMemcpyAsync(jstar, ctx->J_acc, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
+  // S^n goes back in place whatever the copy of j* returns; the copy's
+  // status is checked only after the restore
+  const cudaError_t ce_j =
+      cudaMemcpyAsync(jstar, ctx->J_acc, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st);
   if ((e = state_restore(ctx, snap.p, np, steps0, sort0, E00))) return e;
+  CK(ce_j);
+  CK(cudaStreamSynchronize(ctx->st));
   // 2. the map evaluation at (j*, S^n): records, then vbar and its Jacobians
   const StepConst sc = [&] {
     double tr, ta, itr, ita;

@@ -84,3 +84,35 @@ def test_outer_iteration_limit_fails_and_keeps_the_state():
     r = s.step(1e-28)  # the inner solves pass at 1e-10; the outer test cannot
     assert r["status"] == pic.PIC_EOUTER and 1 <= r["outer_iters"] <= 2
     assert s.checkpoint() == before
+
+
+@pytest.mark.parametrize("bad_index", [-1, 2])
+def test_device_species_out_of_range_is_refused(bad_index):
+    """A species index outside [0, nspecies) in a DEVICE array is refused by
+    the loading kernel (which stores 0 in its place, so no kernel ever
+    indexes the species tables with it): PIC_EARG, and the context is left
+    empty and unstarted, so a step before a valid load and pic_start is
+    refused with PIC_ESTATE."""
+    import torch
+    cfg = small_2d()
+    assert len(cfg["species"]) == 1
+    s = make_gpu(cfg)
+    s.start()
+    dev = lambda a, t=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=t,
+                                                     device="cuda")
+    sp = np.zeros(cfg["w"].shape[0], np.int32)
+    sp[len(sp) // 3] = bad_index
+    with pytest.raises(pic.PicError) as ei:
+        s.set_particles(dev(cfg["x"]), dev(cfg["u"]), dev(cfg["w"]), dev(sp, torch.int32),
+                        on_device=True)
+    assert ei.value.code == pic.PIC_EARG
+    assert s.num_particles() == 0
+    with pytest.raises(pic.PicError) as ei:
+        s.step(1e-12)
+    assert ei.value.code == pic.PIC_ESTATE
+    # a valid load afterwards works as usual
+    s.set_particles(cfg["x"], cfg["u"], cfg["w"], cfg["sp"])
+    s.set_potentials(cfg["A"], cfg["U"])
+    s.start()
+    assert s.step(1e-12)["status"] == 0
+    s.close()
