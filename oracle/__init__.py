@@ -48,8 +48,14 @@ class _Params(C.Structure):
         ("beta", C.c_double), ("lambda_", C.c_double), ("decrease_coef", C.c_double),
         ("growth_limit", C.c_double), ("tol_abs_ratio", C.c_double), ("inner_tol_scale", C.c_double),
         ("nspecies", C.c_int), ("q", C.c_double * 4), ("m", C.c_double * 4),
-        ("order", C.c_int), ("refine_max", C.c_int),
+        ("order", C.c_int), ("refine_max", C.c_int), ("growth_scaled", C.c_int),
     ]
+
+
+class OuterTrace(C.Structure):
+    _fields_ = [("cap", C.c_int), ("j", C.POINTER(C.c_double)), ("srms", C.POINTER(C.c_double)),
+                ("smax", C.POINTER(C.c_double)), ("kind", C.POINTER(C.c_int)),
+                ("alpha", C.POINTER(C.c_double)), ("mh", C.POINTER(C.c_int)), ("n", C.c_int)]
 
 
 class Report(C.Structure):
@@ -115,6 +121,9 @@ def lib():
         L.orc_deposit.argtypes = [C.c_void_p, _D, _D]
         L.orc_eval_particles.argtypes = [C.c_void_p, _D, C.c_double, C.c_long,
                                          C.POINTER(C.c_long), _D, _D, _I]
+        L.orc_scaled_tests.argtypes = [C.c_long, _D, _D, _D, C.c_double, C.c_double, _D, _D]
+        L.orc_outer_affine.argtypes = [C.POINTER(_Params), C.c_long, _D, _D, _D, C.c_double,
+                                       C.POINTER(OuterTrace), C.POINTER(Report)]
     return _lib
 
 
@@ -141,7 +150,8 @@ def _f64(a):
 DEFAULTS = dict(dt=0.1, kappa=1.0, sigma1=1.0, sigma2=1.0, rho_bg=0.0, project=1, gl_points=8,
                 inner_max=64, outer_max=80, anderson_m=4, anderson_start=2, backtrack_levels=7,
                 beta=0.5, lambda_=1e-12, decrease_coef=1e-4, growth_limit=1.2,
-                tol_abs_ratio=0.01, inner_tol_scale=1.0, order=2, refine_max=0)
+                tol_abs_ratio=0.01, inner_tol_scale=1.0, order=2, refine_max=0,
+                growth_scaled=0)
 
 
 def S2(xi: float) -> float:
@@ -194,6 +204,50 @@ def push(Pn, Am, Ap, gphi, D, vbar, q, m, kappa, dt):
     lib().orc_push(*[_p(a) for a in args], float(q), float(m), float(kappa), float(dt),
                    *[_p(o) for o in outs])
     return dict(pminus=outs[0], pplus=outs[1], Pnp1=outs[2], vnew=outs[3])
+
+
+def scaled_tests(r, H, j, tau_r, tau_a):
+    """Eq. mixed-nonlinear-tests on mesh vectors of 3 components per node,
+    component-major (3 x Ng): (scaled RMS, scaled maximum-node residual)."""
+    r, H, j = _f64(r).reshape(-1), _f64(H).reshape(-1), _f64(j).reshape(-1)
+    srms, smax = C.c_double(), C.c_double()
+    lib().orc_scaled_tests(r.size // 3, _p(r), _p(H), _p(j), float(tau_r), float(tau_a),
+                           C.byref(srms), C.byref(smax))
+    return srms.value, smax.value
+
+
+def outer_affine(M, b, j0, tol, trace_cap=0, **opts):
+    """The outer solve of Algorithm 1 (the code orc_step runs) on the affine
+    map H(j) = M j + b over 3 Ng components.  Returns (status, last iterate,
+    report, trace); trace holds per outer iteration the iterate its tests ran
+    at, its scaled residuals, the accepted direction kind (0 Picard, 1
+    Anderson, 2 Picard after a rejected Anderson direction, -1 none), the
+    accepted step length and the history size after the update."""
+    M = _f64(M)
+    b = _f64(b).reshape(-1)
+    j = _f64(j0).reshape(-1).copy()
+    N3 = b.size
+    assert N3 % 3 == 0 and M.shape == (N3, N3)
+    prm = _Params()
+    for k, v in {**DEFAULTS, **opts}.items():
+        if hasattr(prm, k):
+            setattr(prm, k, v)
+    tr = OuterTrace()
+    cap = int(trace_cap)
+    buf = dict(j=np.zeros((max(cap, 1), N3)), srms=np.zeros(max(cap, 1)),
+               smax=np.zeros(max(cap, 1)), kind=np.zeros(max(cap, 1), np.int32),
+               alpha=np.zeros(max(cap, 1)), mh=np.zeros(max(cap, 1), np.int32))
+    tr.cap = cap
+    for k in ("j", "srms", "smax", "alpha"):
+        setattr(tr, k, buf[k].ctypes.data_as(_D))
+    for k in ("kind", "mh"):
+        setattr(tr, k, buf[k].ctypes.data_as(_I))
+    rep = Report()
+    st = lib().orc_outer_affine(C.byref(prm), N3 // 3, _p(M), _p(b), _p(j), float(tol),
+                                C.byref(tr), C.byref(rep))
+    n = tr.n
+    trace = {k: v[:n] for k, v in buf.items()}
+    return st, j, rep.as_dict(), trace
 
 
 class Oracle:

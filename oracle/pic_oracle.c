@@ -644,7 +644,8 @@ void orc_push(const double *Pn, const double *Am, const double *Ap, const double
 void *orc_create(const orc_params *prm) {
   if (!prm || prm->dim < 1 || prm->dim > 3 || prm->nspecies < 1 ||
       prm->nspecies > ORC_MAX_SPECIES || prm->gl_points < 1 || prm->gl_points > GLMAX ||
-      (prm->order != 1 && prm->order != 2) || prm->refine_max < 0 || prm->refine_max > REFMAX)
+      (prm->order != 1 && prm->order != 2) || prm->refine_max < 0 || prm->refine_max > REFMAX ||
+      prm->anderson_m < 0 || prm->anderson_m > ORC_MAX_ANDERSON)
     return NULL;
   orc *o = (orc *)calloc(1, sizeof(orc));
   o->p = *prm;
@@ -1328,16 +1329,19 @@ int orc_eval_map(void *h, const double *j, double tol, double *H, double *vbar,
 /* ------------------------------------------------------------------ */
 /* outer acceptance tests, Eq. mixed-nonlinear-tests                  */
 /* ------------------------------------------------------------------ */
-static double rms3(const orc *o, const double *v) {
+static double rms_n(size_t N3, const double *v) {
   double s = 0.0;
-  for (size_t k = 0; k < (size_t)3 * o->Ng; k++) s += v[k] * v[k];
-  return sqrt(s / (3.0 * o->Ng));
+  for (size_t k = 0; k < N3; k++) s += v[k] * v[k];
+  return sqrt(s / (double)N3);
 }
 
-static void scaled_tests(const orc *o, const double *r, const double *H, const double *j,
-                         double tau_r, double tau_a, double *srms, double *smax) {
-  size_t Ng = (size_t)o->Ng;
-  *srms = rms3(o, r) / (tau_a + 0.5 * tau_r * (rms3(o, H) + rms3(o, j)));
+/* Eq. mixed-nonlinear-tests: the scaled RMS test and the scaled maximum-node
+   test.  Ng nodes, 3 components per node stored component-major (c*Ng + g);
+   |.| of a node is the Euclidean norm of its 3 components. */
+void orc_scaled_tests(long Ng_l, const double *r, const double *H, const double *j,
+                      double tau_r, double tau_a, double *srms, double *smax) {
+  size_t Ng = (size_t)Ng_l, N3 = 3 * Ng;
+  *srms = rms_n(N3, r) / (tau_a + 0.5 * tau_r * (rms_n(N3, H) + rms_n(N3, j)));
   double mx = 0.0;
   for (size_t g = 0; g < Ng; g++) {
     double rr = 0.0, hh = 0.0, jj = 0.0;
@@ -1381,21 +1385,45 @@ static int small_solve(int m, double *Amat, double *b) {
 }
 
 /* ------------------------------------------------------------------ */
-/* one implicit step, Algorithm 1                                      */
+/* the outer solve of Algorithm 1 on a map H(j) given as a callback   */
 /* ------------------------------------------------------------------ */
-int orc_step(void *h, double tol, orc_report *rep) {
-  orc *o = (orc *)h;
-  if (!o->started) return ORC_EARG;
-  size_t n = (size_t)o->np, Ng = (size_t)o->Ng, N3 = 3 * Ng;
-  double tau_r = tol, tau_a = tol * o->p.tol_abs_ratio;
-  double ti_r = tol * o->p.inner_tol_scale, ti_a = ti_r * o->p.tol_abs_ratio;
-  int M = o->p.anderson_m;
-  orc_report R;
-  memset(&R, 0, sizeof R);
+/* map(user, j, H, final_pass): H = H(j); returns ORC_OK or ORC_EINNER */
+typedef int (*outer_map_fn)(void *user, const double *j, double *H, int final_pass);
 
-  step_start(o);
-  double *j = (double *)malloc(sizeof(double) * N3);
-  double *H = (double *)malloc(sizeof(double) * N3);
+static void trace_put(orc_outer_trace *tr, int k, const double *j, size_t N3, double srms,
+                      double smax) {
+  if (!tr || k >= tr->cap) return;
+  if (tr->j) memcpy(tr->j + (size_t)k * N3, j, sizeof(double) * N3);
+  if (tr->srms) tr->srms[k] = srms;
+  if (tr->smax) tr->smax[k] = smax;
+  if (tr->kind) tr->kind[k] = -1;
+  if (tr->alpha) tr->alpha[k] = 0.0;
+  if (tr->mh) tr->mh[k] = 0;
+  tr->n = k + 1;
+}
+
+/* Converges H(j) = j from the trial current j (Algorithm 1): at every outer
+   iteration the tests of Eq. mixed-nonlinear-tests; when both pass, one more
+   evaluation at the same j (final_pass = 1) that must pass them again;
+   otherwise a direction, type-II Anderson (Eq. anderson-type-two-update) once
+   the iteration is eligible and history exists, else damped Picard beta r,
+   with backtracking alpha = 1, 1/2, .. (backtrack_levels values) under the
+   sufficient-decrease and maximum-node safeguards; a rejected Anderson
+   direction is retried as damped Picard.  The accepted trial's evaluation
+   gives the next iterate's H(j).  History: the differences of successive
+   accepted (j, r), at most anderson_m columns (oldest dropped), cleared when
+   the regularised Gram system has no finite solution or when the RMS
+   residual grows by more than growth_limit (reading R8; growth_scaled
+   selects the scaled RMS of Eq. mixed-nonlinear-tests instead of the plain
+   RMS).  On return j holds the last iterate and H its map value (the
+   verification's, on success).  R receives outer_iters (the iterations
+   begun, counting the one whose tests pass), map_evals and the scaled
+   residuals. */
+static int outer_solve(const orc_params *p, size_t Ng, outer_map_fn map, void *user,
+                       double tau_r, double tau_a, double *j, double *H, orc_report *R,
+                       orc_outer_trace *tr) {
+  size_t N3 = 3 * Ng;
+  int M = p->anderson_m;
   double *r = (double *)malloc(sizeof(double) * N3);
   double *jt = (double *)malloc(sizeof(double) * N3);
   double *Ht = (double *)malloc(sizeof(double) * N3);
@@ -1404,37 +1432,35 @@ int orc_step(void *h, double tol, orc_report *rep) {
   double *dJ = (double *)calloc((size_t)(M > 0 ? M : 1) * N3, sizeof(double));
   double *dR = (double *)calloc((size_t)(M > 0 ? M : 1) * N3, sizeof(double));
   int mh = 0;
-  eval_t e;
-  eval_alloc(o, &e);
-  memcpy(j, o->J, sizeof(double) * N3);
-  int status = map_eval(o, j, ti_r, ti_a, &e, H, 0);
-  R.map_evals = 1;
-  for (size_t k = 0; k < N3; k++) r[k] = H[k] - j[k];
-  int k;
+  if (tr) tr->n = 0;
+  int status = map(user, j, H, 0);
+  R->map_evals = 1;
+  for (size_t q = 0; q < N3; q++) r[q] = H[q] - j[q];
   int done = 0;
-  for (k = 0; status == ORC_OK && k < o->p.outer_max; k++) {
+  for (int k = 0; status == ORC_OK && k < p->outer_max; k++) {
     double srms, smax;
-    scaled_tests(o, r, H, j, tau_r, tau_a, &srms, &smax);
-    R.outer_iters = k + 1;
-    R.res_scaled_rms = srms;
-    R.res_scaled_max = smax;
+    orc_scaled_tests((long)Ng, r, H, j, tau_r, tau_a, &srms, &smax);
+    R->outer_iters = k + 1;
+    R->res_scaled_rms = srms;
+    R->res_scaled_max = smax;
+    trace_put(tr, k, j, N3, srms, smax);
     if (srms <= 1.0 && smax <= 1.0) {
       /* verify by re-evaluating the map at the candidate current */
-      status = map_eval(o, j, ti_r, ti_a, &e, H, 1);
-      R.map_evals++;
+      status = map(user, j, H, 1);
+      R->map_evals++;
       if (status != ORC_OK) break;
       for (size_t q = 0; q < N3; q++) r[q] = H[q] - j[q];
-      scaled_tests(o, r, H, j, tau_r, tau_a, &srms, &smax);
-      R.res_scaled_rms = srms;
-      R.res_scaled_max = smax;
+      orc_scaled_tests((long)Ng, r, H, j, tau_r, tau_a, &srms, &smax);
+      R->res_scaled_rms = srms;
+      R->res_scaled_max = smax;
       if (!(srms <= 1.0 && smax <= 1.0)) { status = ORC_EOUTER; break; }
       done = 1;
       break;
     }
     /* proposed directions: Anderson (type II) when eligible, else Picard */
     int have_anderson = 0;
-    if (k >= o->p.anderson_start && mh > 0) {
-      double G[16], b[4], tr = 0.0;
+    if (k >= p->anderson_start && mh > 0) {
+      double G[ORC_MAX_ANDERSON * ORC_MAX_ANDERSON], b[ORC_MAX_ANDERSON], trg = 0.0;
       for (int a = 0; a < mh; a++) {
         for (int c = 0; c < mh; c++) {
           double s = 0.0;
@@ -1444,36 +1470,37 @@ int orc_step(void *h, double tol, orc_report *rep) {
         double s = 0.0;
         for (size_t q = 0; q < N3; q++) s += dR[a * N3 + q] * r[q];
         b[a] = s;
-        tr += G[a * mh + a];
+        trg += G[a * mh + a];
       }
-      for (int a = 0; a < mh; a++) G[a * mh + a] += o->p.lambda * tr / mh;
-      if (isfinite(tr) && tr > 0.0 && small_solve(mh, G, b) == 0) {
+      for (int a = 0; a < mh; a++) G[a * mh + a] += p->lambda * trg / mh;
+      if (isfinite(trg) && trg > 0.0 && small_solve(mh, G, b) == 0) {
         have_anderson = 1;
         for (size_t q = 0; q < N3; q++) {
-          double s = o->p.beta * r[q];
-          for (int a = 0; a < mh; a++) s -= (dJ[a * N3 + q] + o->p.beta * dR[a * N3 + q]) * b[a];
+          double s = p->beta * r[q];
+          for (int a = 0; a < mh; a++) s -= (dJ[a * N3 + q] + p->beta * dR[a * N3 + q]) * b[a];
           dir[q] = s; /* j_A - j */
         }
       } else {
         mh = 0; /* unusable history */
       }
     }
-    int accepted = 0;
+    int accepted = 0, kind = 0;
+    double alpha_ok = 0.0, srt = 0.0, smt = 0.0;
     for (int attempt = have_anderson ? 0 : 1; attempt < 2 && !accepted; attempt++) {
       if (attempt == 1)
-        for (size_t q = 0; q < N3; q++) dir[q] = o->p.beta * r[q];
+        for (size_t q = 0; q < N3; q++) dir[q] = p->beta * r[q];
       double alpha = 1.0;
-      for (int lvl = 0; lvl < o->p.backtrack_levels; lvl++, alpha *= 0.5) {
+      for (int lvl = 0; lvl < p->backtrack_levels; lvl++, alpha *= 0.5) {
         for (size_t q = 0; q < N3; q++) jt[q] = j[q] + alpha * dir[q];
-        status = map_eval(o, jt, ti_r, ti_a, &e, Ht, 0);
-        R.map_evals++;
+        status = map(user, jt, Ht, 0);
+        R->map_evals++;
         if (status != ORC_OK) break;
         for (size_t q = 0; q < N3; q++) rt[q] = Ht[q] - jt[q];
-        double srt, smt;
-        scaled_tests(o, rt, Ht, jt, tau_r, tau_a, &srt, &smt);
-        if (srt <= (1.0 - o->p.decrease_coef * alpha) * srms &&
-            smt <= o->p.growth_limit * smax) {
+        orc_scaled_tests((long)Ng, rt, Ht, jt, tau_r, tau_a, &srt, &smt);
+        if (srt <= (1.0 - p->decrease_coef * alpha) * srms && smt <= p->growth_limit * smax) {
           accepted = 1;
+          alpha_ok = alpha;
+          kind = attempt == 0 ? 1 : (have_anderson ? 2 : 0);
           break;
         }
       }
@@ -1481,7 +1508,7 @@ int orc_step(void *h, double tol, orc_report *rep) {
     }
     if (status != ORC_OK) break;
     if (!accepted) { status = ORC_EOUTER; break; }
-    /* history update; clear when the residual grew too much */
+    /* history update; cleared when the residual grew too much */
     if (M > 0) {
       if (mh == M) {
         memmove(dJ, dJ + N3, sizeof(double) * (size_t)(M - 1) * N3);
@@ -1493,13 +1520,90 @@ int orc_step(void *h, double tol, orc_report *rep) {
         dR[mh * N3 + q] = rt[q] - r[q];
       }
       mh++;
-      if (rms3(o, rt) > o->p.growth_limit * rms3(o, r)) mh = 0;
+      double grown = p->growth_scaled ? srt / srms : rms_n(N3, rt) / rms_n(N3, r);
+      if (grown > p->growth_limit) mh = 0;
+    }
+    if (tr && k < tr->cap) {
+      if (tr->kind) tr->kind[k] = kind;
+      if (tr->alpha) tr->alpha[k] = alpha_ok;
+      if (tr->mh) tr->mh[k] = mh;
     }
     memcpy(j, jt, sizeof(double) * N3);
     memcpy(H, Ht, sizeof(double) * N3);
     memcpy(r, rt, sizeof(double) * N3);
   }
   if (status == ORC_OK && !done) status = ORC_EOUTER;
+  free(r); free(jt); free(Ht); free(rt); free(dir); free(dJ); free(dR);
+  return status;
+}
+
+/* the particle map of one step as the outer solve's callback */
+typedef struct {
+  orc *o;
+  eval_t *e;
+  double ti_r, ti_a;
+} particle_map_t;
+
+static int particle_map(void *user, const double *j, double *H, int final_pass) {
+  particle_map_t *pm = (particle_map_t *)user;
+  return map_eval(pm->o, j, pm->ti_r, pm->ti_a, pm->e, H, final_pass);
+}
+
+/* an affine stand-in map H(j) = M j + b (test support) */
+typedef struct {
+  size_t N3;
+  const double *M, *b;
+} affine_map_t;
+
+static int affine_map(void *user, const double *j, double *H, int final_pass) {
+  (void)final_pass;
+  affine_map_t *am = (affine_map_t *)user;
+  for (size_t a = 0; a < am->N3; a++) {
+    double s = am->b[a];
+    for (size_t c = 0; c < am->N3; c++) s += am->M[a * am->N3 + c] * j[c];
+    H[a] = s;
+  }
+  return ORC_OK;
+}
+
+int orc_outer_affine(const orc_params *prm, long Ng, const double *M, const double *b,
+                     double *j, double tol, orc_outer_trace *tr, orc_report *rep) {
+  if (!prm || Ng < 1 || !M || !b || !j || prm->anderson_m < 0 ||
+      prm->anderson_m > ORC_MAX_ANDERSON)
+    return ORC_EARG;
+  size_t N3 = 3 * (size_t)Ng;
+  affine_map_t am = {N3, M, b};
+  orc_report R;
+  memset(&R, 0, sizeof R);
+  double *H = (double *)malloc(sizeof(double) * N3);
+  int st = outer_solve(prm, (size_t)Ng, affine_map, &am, tol, tol * prm->tol_abs_ratio, j, H, &R,
+                       tr);
+  free(H);
+  R.status = st;
+  if (rep) *rep = R;
+  return st;
+}
+
+/* ------------------------------------------------------------------ */
+/* one implicit step, Algorithm 1                                      */
+/* ------------------------------------------------------------------ */
+int orc_step(void *h, double tol, orc_report *rep) {
+  orc *o = (orc *)h;
+  if (!o->started) return ORC_EARG;
+  size_t n = (size_t)o->np, Ng = (size_t)o->Ng, N3 = 3 * Ng;
+  double tau_r = tol, tau_a = tol * o->p.tol_abs_ratio;
+  double ti_r = tol * o->p.inner_tol_scale, ti_a = ti_r * o->p.tol_abs_ratio;
+  orc_report R;
+  memset(&R, 0, sizeof R);
+
+  step_start(o);
+  double *j = (double *)malloc(sizeof(double) * N3);
+  double *H = (double *)malloc(sizeof(double) * N3);
+  eval_t e;
+  eval_alloc(o, &e);
+  memcpy(j, o->J, sizeof(double) * N3);
+  particle_map_t pm = {o, &e, ti_r, ti_a};
+  int status = outer_solve(&o->p, Ng, particle_map, &pm, tau_r, tau_a, j, H, &R, NULL);
 
   if (status == ORC_OK) {
     /* commit: x^{n+1} = x^n + dt vbar, P^{n+1}, fields at n+1, J^{n+1/2} */
@@ -1542,7 +1646,7 @@ int orc_step(void *h, double tol, orc_report *rep) {
   R.status = status;
   if (rep) *rep = R;
   eval_free(&e);
-  free(j); free(H); free(r); free(jt); free(Ht); free(rt); free(dir); free(dJ); free(dR);
+  free(j); free(H);
   return status;
 }
 

@@ -26,6 +26,7 @@ extern "C" {
 #endif
 
 #define ORC_MAX_SPECIES 4
+#define ORC_MAX_ANDERSON 8
 
 typedef struct {
   int dim;            /* active spatial dimensions, 1..3 */
@@ -46,7 +47,27 @@ typedef struct {
   int refine_max;     /* convergence-triggered particle refinement (Sec. 5.3):
                          a particle whose solve fails is retried with 2, 4, ..
                          2^refine_max equal substeps; 0 = off */
+  int growth_scaled;  /* Anderson history clearing (Sec. 4.5, reading R8): 0
+                         compares plain RMS residuals of successive iterates,
+                         1 the scaled RMS of Eq. mixed-nonlinear-tests */
 } orc_params;
+
+/* Per-iteration record of the outer solve (test support): entry k describes
+   outer iteration k (0-based).  j: the iterate at which its tests ran
+   (cap * 3Ng doubles, may be NULL); srms, smax: its scaled residuals;
+   kind: the accepted direction (0 damped Picard, 1 Anderson, 2 damped
+   Picard after a rejected Anderson direction; -1 none: the tests passed or
+   the step failed); alpha: the accepted step length; mh: history columns
+   after the update.  n receives the number of entries written. */
+typedef struct {
+  int cap;
+  double *j;
+  double *srms, *smax;
+  int *kind;
+  double *alpha;
+  int *mh;
+  int n;
+} orc_outer_trace;
 
 typedef struct {
   double W, K, E_tot, rel_dE;
@@ -95,6 +116,19 @@ int orc_knot_jumps(void *h, double eps, double *E_jump, double *G_jump);
 int orc_set_state(void *h, long np, const int *species, const double *x, const double *P,
                   const double *w, const double *phi, const double *psi, const double *A,
                   const double *U, const double *rho, const double *J);
+
+/* The tests of Eq. mixed-nonlinear-tests on Ng nodes of 3 components
+   (component-major): scaled RMS and scaled maximum-node residual. */
+void orc_scaled_tests(long Ng, const double *r, const double *H, const double *j,
+                      double tau_r, double tau_a, double *srms, double *smax);
+
+/* The outer solve of Algorithm 1 (the same code orc_step runs) on the affine
+   stand-in map H(j) = M j + b, M row-major 3Ng x 3Ng: j holds the initial
+   trial current and returns the last iterate; tau_rel = tol, tau_abs =
+   tol * tol_abs_ratio; only the outer-solver fields of prm are read.  tr
+   (may be NULL) records each iteration. */
+int orc_outer_affine(const orc_params *prm, long Ng, const double *M, const double *b,
+                     double *j, double tol, orc_outer_trace *tr, orc_report *rep);
 
 /* unit-level pieces, exposed so that tests can pin them one by one */
 double orc_S2(double xi);
