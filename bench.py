@@ -13,7 +13,9 @@ T = 0.01, dt = 0.05, tolerance 1e-10; FP64 path (value) and FP32-mixed path
 (reported beside it).  Inputs are generated once (seeded), resident in HBM
 before the timed region; L2 is flushed between timed steps.
 
-The line also carries the batched ensemble ("ensemble"): 256 independent 1D3V
+The line also carries the 1D3V two-stream run in full ("two_stream_1d": 64
+cells, 4,096 particles, FP64, tol 1e-12, all 200 steps), the batched ensemble
+("ensemble"): 256 independent 1D3V
 two-stream instances of uneven sizes advanced by one pic_batch (FP32-mixed and
 FP64), against the plain FP64 path (one context per instance, stepped in turn),
 and the large case ("large"): 512^2 Weibel with mobile ions, 67,108,864
@@ -239,6 +241,57 @@ def run_ensemble(args, rank, barrier, flush, stream):
     return out, sum(nps)
 
 
+# ---------------------------------------------------------------- 1D two-stream run
+TWO_STREAM = "two_stream_1d_64cells_4096p_200steps"
+
+
+def run_two_stream_1d(args, barrier, flush, stream, peak64):
+    """The 1D3V cold relativistic two-stream run in full: 64 cells on
+    L = 4 pi, beams u_x = +-0.6 with 32 particles per cell each (4,096
+    particles), density seed 1e-3, dt = 0.1, tol 1e-12, FP64, 200 steps, every
+    step timed (CUDA events on the library's stream).  A problem this small
+    occupies 32 of the GPU's 148 SMs for a few microseconds per launch, so
+    the step is launch- and latency-bound; the roofline fraction says so."""
+    import torch
+
+    import paper_2609_36383_b300 as P
+    import pic_inputs
+    cfg = pic_inputs.two_stream_1d(nx=64, ppc_beam=32)
+    npart = cfg["w"].shape[0]
+    sim = P.from_config(cfg, precision=P.PIC_FP64)
+    sim.start()
+    barrier()
+    ms, pushes, drift, outer, evals = 0.0, 0, 0.0, [], []
+    for _ in range(200):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = sim.step(cfg["tol"], raise_on_fail=True)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        pushes += npart * r["map_evals"]
+        drift = max(drift, abs(r["rel_dE"]))
+        outer.append(r["outer_iters"])
+        evals.append(r["map_evals"])
+    barrier()
+    st = sim.stats()
+    sim.close()
+    avg = st["map_ms"] / max(st["map_launches"], 1)
+    ach = algorithmic_flops(1, st) / max(st["map_launches"], 1) / (avg * 1e-3)
+    return {"workload": TWO_STREAM, "particles": npart, "steps": 200, "value": pushes / (ms * 1e-3),
+            "unit": UNIT, "dtype": "f64", "ms_per_step": ms / 200, "tol": cfg["tol"],
+            "max_abs_rel_dE": drift, "mean_outer_iters": statistics.mean(outer),
+            "max_outer_iters": max(outer), "mean_map_evals_per_step": statistics.mean(evals),
+            "mean_inner_iters": st["inner_iters"] / max(st["pushes"], 1),
+            "l2": "flushed before every step (256 MiB write)",
+            "map_kernel": {"share_of_step": st["map_ms"] / max(ms, 1e-9),
+                           "achieved_tflops": ach / 1e12, "peak_tflops": peak64 / 1e12,
+                           "frac": ach / peak64, "avg_ms": avg,
+                           "bound": "launch/latency (32 CTAs of 128 threads)"}}
+
+
 # ---------------------------------------------------------------- large case
 LARGE = "weibel_2d_ions_512x512_256ppc"
 
@@ -379,8 +432,9 @@ def run_ours(args):
             fp64_sim = sim
         else:
             sim.close()
-    ens = lg = None
+    ens = lg = ts1 = None
     if not (args.only or args.skip_e2e):
+        ts1 = run_two_stream_1d(args, barrier, flush, stream, P.fma_throughput(P.PIC_FP64))
         ens, ens_particles = run_ensemble(args, rank, barrier, flush, stream)
         if not args.no_large:
             lg = run_large(args, rank, barrier, flush, stream)
@@ -510,6 +564,7 @@ def run_ours(args):
                     "peak_source": hbm_src,
                     "frac": bytes_launch / (avg_ms * 1e-3) / 1e9 / hbm},
         },
+        "two_stream_1d": ts1,
         "ensemble": ensemble_summary(dist, ens, ens_particles, args.steps),
         "large": large_summary(dist, lg, args.steps, peak32) if lg else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

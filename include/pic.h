@@ -74,7 +74,13 @@ typedef struct {
   int gl_points;                /* Gauss-Legendre points per knot-split orbit piece;
                                    0 = minimal exact count dim+1 */
   int inner_max, outer_max;
-  int anderson_m, anderson_start, backtrack_levels;
+  int anderson_m;               /* Anderson history columns M */
+  int anderson_start;           /* m_A: outer iterations are counted from 1, and the first
+                                   that may take an Anderson direction is iteration m_A
+                                   (earlier ones, and any without history, take damped
+                                   Picard); pic_report.outer_iters counts the iterations
+                                   begun, the last being the one whose tests passed */
+  int backtrack_levels;
   double beta, lambda, decrease_coef, growth_limit;
   double tol_abs_ratio;         /* tau_abs = tol * tol_abs_ratio (tau_rel = tol) */
   double inner_tol_scale;       /* inner tolerance = outer tolerance * this */
@@ -110,7 +116,33 @@ typedef struct {
                                    with at least 8 nodes per active dimension only
                                    (pic_init returns PIC_EARG otherwise), and not in a
                                    batch (pic_batch_init rejects it); default 0 */
+  int growth_scaled;            /* Anderson history clearing (Sec. 4.5): the history is
+                                   cleared when the RMS residual of an accepted iterate
+                                   exceeds growth_limit times the previous one; 0
+                                   (default) compares plain RMS residuals, 1 the scaled
+                                   RMS residuals of Eq. mixed-nonlinear-tests */
+  int host_control;             /* 0 (default): Algorithm 1's decisions are taken on the
+                                   device, and a step's whole outer iteration runs as two
+                                   CUDA graph launches with one synchronisation at the
+                                   end; 1: the host takes them, synchronising after every
+                                   map evaluation (the same decisions, for checks) */
+  int nonlinear_solver;         /* PIC_SOLVER_ANDERSON (default): Algorithm 1's type-II
+                                   Anderson iteration; PIC_SOLVER_NEWTON_KRYLOV: inexact
+                                   Newton on H(j) - j = 0, each direction from
+                                   (I - H'(j)) d = r by GMRES(20) on Jacobian-vector
+                                   products (dual-number map evaluations, as
+                                   pic_eval_map_jvp), forcing terms of Eisenstat and
+                                   Walker (choice 2, gamma 0.9) bounded below by half the
+                                   reduction the outer tests still need, the same
+                                   backtracking, tests and verifying evaluation as
+                                   Algorithm 1.  FP64 contexts with quadratic shapes, no
+                                   refinement, the cold inner start and the atomic deposit
+                                   (pic_init returns PIC_EARG otherwise); the host drives
+                                   the iteration */
 } pic_options;
+
+#define PIC_SOLVER_ANDERSON 0
+#define PIC_SOLVER_NEWTON_KRYLOV 1
 
 /* Per-step report (Sec. 4.4 diagnostics and solver counters). */
 typedef struct {
@@ -125,6 +157,8 @@ typedef struct {
   int status;                   /* return code of the step */
   int refined;                  /* particles of the final map evaluation that needed
                                    substeps (refine_max > 0) */
+  int jvp_evals;                /* Jacobian-vector products (dual-number map
+                                   evaluations) of the Newton-Krylov solver; 0 otherwise */
 } pic_report;
 
 /* Fill *opt with the paper's defaults (see pic_options). */
@@ -150,6 +184,21 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species,
 int pic_set_particles(pic_ctx *ctx, int64_t n, const int32_t *species,
                       const double *x, const double *u_or_P, int is_canonical,
                       const double *w, int on_device);
+
+/* pic_set_particles with positions in the form the library stores them
+   (Sec. 2.4: the nearest node plus the offset from it): cell holds dim*N
+   node indices (row l: 0 <= cell < n[l]) and offset dim*N offsets in node
+   units, -1/2 <= offset < 1/2; the position along l is
+   x0[l] + (cell + offset) * L[l] / n[l].  Particles that should see
+   identical arithmetic in different cells (quiet starts, symmetry tests)
+   get bit-identical offsets this way, which absolute coordinates far from
+   the origin cannot give.  An index or offset out of range returns
+   PIC_EARG (host arrays are checked before anything is copied, device
+   arrays by the loading kernel) and leaves the context empty and
+   unstarted.  Everything else is as for pic_set_particles. */
+int pic_set_particles_local(pic_ctx *ctx, int64_t n, const int32_t *species,
+                            const int32_t *cell, const double *offset, const double *u_or_P,
+                            int is_canonical, const double *w, int on_device);
 
 /* Initial vector potential A and its time derivative U (3*Ng each; NULL =
    zero).  Both are projected by pic_start. */

@@ -20,7 +20,9 @@
  *      the paper reports for the final evaluation of each step);
  *   R6 inner test: max_c |vnew_c - v_c| <= tau_abs + tau_rel max_c |vnew_c|;
  *   R7 the deposit uses the final orbit velocity and its own orbit weights;
- *   R8 Anderson: Picard (j + beta r) before iteration anderson_start,
+ *   R8 Anderson: iterations are counted from 1, and iteration m_A
+ *      (anderson_start) is the first that may take an Anderson direction;
+ *      before it, and whenever no history exists, damped Picard (j + beta r);
  *      history cleared when the regularised Gram solve is not finite or the
  *      unscaled RMS residual grows by more than growth_limit;
  *   R9 tau_rel = tol, tau_abs = tol * tol_abs_ratio;
@@ -1459,7 +1461,7 @@ static int outer_solve(const orc_params *p, size_t Ng, outer_map_fn map, void *u
     }
     /* proposed directions: Anderson (type II) when eligible, else Picard */
     int have_anderson = 0;
-    if (k >= p->anderson_start && mh > 0) {
+    if (k + 1 >= p->anderson_start && mh > 0) {  /* iterations counted from 1 */
       double G[ORC_MAX_ANDERSON * ORC_MAX_ANDERSON], b[ORC_MAX_ANDERSON], trg = 0.0;
       for (int a = 0; a < mh; a++) {
         for (int c = 0; c < mh; c++) {

@@ -22,9 +22,11 @@ PIC_OK, PIC_EARG, PIC_ENOMEM, PIC_ECUDA, PIC_EINNER, PIC_EOUTER, PIC_ESTATE = 0,
 PIC_ETOOBIG = -7
 NOALLOC_MAX_PARTICLES = 16384 * 256
 PIC_FP64, PIC_MIXED = 0, 1
+PIC_SOLVER_ANDERSON, PIC_SOLVER_NEWTON_KRYLOV = 0, 1
 
 # every symbol include/pic.h declares (checked by the CPU test suite)
-EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_potentials",
+EXPORTS = ("pic_default_options", "pic_init", "pic_set_particles", "pic_set_particles_local",
+           "pic_set_potentials",
            "pic_start", "pic_step", "pic_eval_map", "pic_eval_map_jvp", "pic_eval_map_vjp", "pic_step_vjp", "pic_tune_sort",
            "pic_tangent_begin", "pic_tangent_end", "pic_get_tangent", "pic_num_particles", "pic_get_particles",
            "pic_get_velocities", "pic_get_potentials", "pic_set_state", "pic_checkpoint_bytes",
@@ -54,6 +56,7 @@ class Options(C.Structure):
         ("inner_tol_scale", C.c_double), ("precision", C.c_int), ("mixed_tol_floor", C.c_double),
         ("sort_every", C.c_int), ("cuda_stream", C.c_void_p), ("inner_warm_start", C.c_int),
         ("order", C.c_int), ("refine_max", C.c_int), ("deterministic_deposit", C.c_int),
+        ("growth_scaled", C.c_int), ("host_control", C.c_int), ("nonlinear_solver", C.c_int),
     ]
 
 
@@ -98,6 +101,7 @@ class Report(C.Structure):
         ("chain_rms", C.c_double), ("res_scaled_rms", C.c_double), ("res_scaled_max", C.c_double),
         ("outer_iters", C.c_int), ("map_evals", C.c_int), ("inner_max", C.c_int),
         ("inner_mean", C.c_double), ("status", C.c_int), ("refined", C.c_int),
+        ("jvp_evals", C.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -119,6 +123,8 @@ def lib():
         L.pic_init.argtypes = [C.POINTER(_VP), C.POINTER(Grid), C.POINTER(Species), C.c_int,
                                C.c_double, C.POINTER(Options)]
         L.pic_set_particles.argtypes = [_VP, C.c_int64, _VP, _VP, _VP, C.c_int, _VP, C.c_int]
+        L.pic_set_particles_local.argtypes = [_VP, C.c_int64, _VP, _VP, _VP, _VP, C.c_int, _VP,
+                                              C.c_int]
         L.pic_set_potentials.argtypes = [_VP, _VP, _VP, C.c_int]
         L.pic_start.argtypes = [_VP, C.POINTER(Report)]
         L.pic_step.argtypes = [_VP, C.c_double, C.POINTER(Report)]
@@ -269,6 +275,21 @@ class Simulation:
         self._check(lib().pic_set_particles(self._h, n, _ptr(species, on_device), _ptr(x, on_device),
                                             _ptr(u_or_P, on_device), int(canonical),
                                             _ptr(w, on_device), int(on_device)))
+
+    def set_particles_local(self, cell, offset, u_or_P, w, species=None, canonical=False,
+                            on_device=False):
+        """Particles in the stored form: node index per dimension (dim x N int32)
+        and offset from it in node units in [-1/2, 1/2) (dim x N)."""
+        if not on_device:
+            cell = np.ascontiguousarray(cell, np.int32)
+            offset = np.ascontiguousarray(offset, np.float64)
+            u_or_P = np.ascontiguousarray(u_or_P, np.float64)
+            w = np.ascontiguousarray(w, np.float64)
+            species = None if species is None else np.ascontiguousarray(species, np.int32)
+        n = int(w.shape[0])
+        self._check(lib().pic_set_particles_local(
+            self._h, n, _ptr(species, on_device), _ptr(cell, on_device), _ptr(offset, on_device),
+            _ptr(u_or_P, on_device), int(canonical), _ptr(w, on_device), int(on_device)))
 
     def set_potentials(self, A=None, U=None, on_device=False):
         if not on_device:

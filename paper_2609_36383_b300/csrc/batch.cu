@@ -106,7 +106,7 @@ struct BLoop {
 };
 
 struct BParams {  // solver constants of the batch
-  int M, anderson_start, levels, outer_max;
+  int M, anderson_start, levels, outer_max, growth_scaled;
   double beta, lambda, dc, growth;
   double tr, ta;  // outer tolerances
 };
@@ -321,7 +321,7 @@ __device__ void outer_top(BState &s, const BParams &bp) {
     return;
   }
   bool have = false;
-  if (s.k >= bp.anderson_start && s.mh > 0) {
+  if (s.k + 1 >= bp.anderson_start && s.mh > 0) {  // iterations counted from 1
     const int m = s.mh;
     double A[kMh * kMh], b[kMh], tr_g = 0.0;
     for (int p = 0; p < m; p++) {
@@ -430,7 +430,8 @@ k_bctl(int B, BState *__restrict__ states, const BRes *__restrict__ res,
                   s.g[a] = v;
                 }
               }
-            if (rms > bp.growth * s.T_rms) { s.mh = 0; s.hist0 = 0; }
+            const double grown = bp.growth_scaled ? srms / s.T_srms : rms / s.T_rms;
+            if (grown > bp.growth) { s.mh = 0; s.hist0 = 0; }
           }
           s.T_srms = srms;
           s.T_smax = smax;
@@ -1204,6 +1205,7 @@ BParams b_params(const pic_batch *bt, double tr, double ta) {
   bp.lambda = bt->opt.lambda;
   bp.dc = bt->opt.decrease_coef;
   bp.growth = bt->opt.growth_limit;
+  bp.growth_scaled = bt->opt.growth_scaled;
   bp.tr = tr;
   bp.ta = ta;
   return bp;

@@ -1349,16 +1349,30 @@ __device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i_sl
   }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // FP32 instances: at least 4 resident CTAs (<= 128 registers) to hide latency;
-// FP64 instances are bound by the FP64 pipe and keep their registers
+// FP64 instances are bound by the FP64 pipe and keep their registers.
+// tim (may be null): the launch's first CTA start and last CTA end on the
+// global nanosecond timer, folded in with atomicMin / atomicMax (device-side
+// timing for launches inside a graph loop, where events cannot accumulate).
 template <int D, typename T, bool FINAL, bool GEN>
 __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 4 : 1)
 k_map(PView<T> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
       double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
-      double *__restrict__ psum) {
+      double *__restrict__ psum, unsigned long long *__restrict__ tim) {
+  if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   map_block<D, T, FINAL, GEN>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes, nodes_u, J, pg,
                               kc, ms, cnt, psum + 2 * (size_t)blockIdx.x);
+  if (tim) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(tim + 1, global_ns());
+  }
 }
 
 }  // namespace

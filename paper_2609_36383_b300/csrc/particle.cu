@@ -12,21 +12,39 @@ namespace {
 constexpr int kPsumBlocks = 128, kPsumThreads = 256;
 
 // ---- simple per-particle kernels -------------------------------------------
+// Loads particles.  Positions come either as absolute coordinates x (cin
+// null), from which the nearest node and the offset are formed, or directly
+// in the stored form (cin: nearest node per dimension in [0, n), x: the
+// offset in node units in [-1/2, 1/2)); a stored-form entry out of range is
+// replaced by node 0, offset 0 and reported through *bad (bit 2).
 template <int D, typename T>
 __global__ void k_load(int64_t n, int64_t cap, const double *__restrict__ x,
-                       const double *__restrict__ uP, int canonical, const double *__restrict__ w,
+                       const int32_t *__restrict__ cin, const double *__restrict__ uP,
+                       int canonical, const double *__restrict__ w,
                        const int32_t *__restrict__ sp, int nspecies, PGeom pg, int32_t *cell,
                        T *off, T *P, double *u_in, double *wo, int32_t *spo, int64_t *id,
                        unsigned int *bad) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int l = 0; l < D; l++) {
-    double u = (x[l * n + i] - pg.x0[l]) * pg.inv_dx[l];
-    double nn = (double)pg.n[l];
-    u -= nn * floor(u / nn);
-    int c = (int)floor(u + 0.5);
-    double o = u - (double)c;
-    if (c >= pg.n[l]) c -= pg.n[l];
+    int c;
+    double o;
+    if (cin) {
+      c = cin[l * n + i];
+      o = x[l * n + i];
+      if (c < 0 || c >= pg.n[l] || !(o >= -0.5 && o < 0.5)) {
+        atomicOr(bad, 2u);
+        c = 0;
+        o = 0.0;
+      }
+    } else {
+      double u = (x[l * n + i] - pg.x0[l]) * pg.inv_dx[l];
+      double nn = (double)pg.n[l];
+      u -= nn * floor(u / nn);
+      c = (int)floor(u + 0.5);
+      o = u - (double)c;
+      if (c >= pg.n[l]) c -= pg.n[l];
+    }
     cell[l * cap + i] = c;
     off[l * cap + i] = (T)o;
   }
@@ -377,7 +395,7 @@ int particles_alloc(pic_ctx *ctx, int64_t n) {
   CK(cudaMalloc((void **)&ctx->iters, sizeof(int32_t) * cap));
   CK(cudaMalloc((void **)&ctx->u_in, sizeof(double) * 3 * cap));
   CK(cudaMalloc((void **)&ctx->tmp_d, sizeof(double) * 7 * cap));
-  CK(cudaMalloc((void **)&ctx->tmp_i, sizeof(int32_t) * cap));
+  CK(cudaMalloc((void **)&ctx->tmp_i, sizeof(int32_t) * 4 * cap));
   CK(cudaMalloc((void **)&ctx->keys, sizeof(int32_t) * cap));
   CK(cudaMalloc((void **)&ctx->tmp_l, sizeof(int64_t) * cap));
   CK(cudaMalloc((void **)&ctx->psum, sizeof(double) * (4 * nb + 4 * kPsumBlocks) + 64));
@@ -390,13 +408,18 @@ int particles_alloc(pic_ctx *ctx, int64_t n) {
   return PIC_OK;
 }
 
-int particles_load(pic_ctx *ctx, const int32_t *sp, const double *x, const double *uP,
-                   int canonical, const double *w, int on_device) {
+int particles_load(pic_ctx *ctx, const int32_t *sp, const int32_t *cell_in, const double *x,
+                   const double *uP, int canonical, const double *w, int on_device) {
   int64_t n = ctx->np, cap = ctx->cap;
   if (n == 0) return PIC_OK;
   const int d = ctx->g.dim;
   const double *dx = x, *du = uP, *dw = w;
-  const int32_t *dsp = sp;
+  const int32_t *dsp = sp, *dcell = cell_in;
+  if (cell_in && !on_device) {  // staged after the species staging area
+    CK(cudaMemcpyAsync(ctx->tmp_i + cap, cell_in, sizeof(int32_t) * d * n,
+                       cudaMemcpyHostToDevice, ctx->st));
+    dcell = ctx->tmp_i + cap;
+  }
   if (!on_device) {
     double *stg = ctx->tmp_d;
     CK(cudaMemcpyAsync(stg, x, sizeof(double) * d * n, cudaMemcpyHostToDevice, ctx->st));
@@ -413,15 +436,16 @@ int particles_load(pic_ctx *ctx, const int32_t *sp, const double *x, const doubl
   PGeom pg = pgeom(ctx);
   CK(cudaMemsetAsync(ctx->cnt_dev, 0, sizeof(EvalCounters), ctx->st));
   PIC_DISPATCH(ctx, (k_load<DD, RT><<<nblk(n), kPT, 0, ctx->st>>>(
-                         n, cap, dx, du, canonical, dw, dsp, ctx->nspecies, pg, ctx->cell,
-                         (RT *)ctx->off, (RT *)ctx->P, ctx->u_in, ctx->w, ctx->sp, ctx->id,
-                         &ctx->cnt_dev->status)));
+                         n, cap, dx, dcell, du, canonical, dw, dsp,
+                         ctx->nspecies, pg, ctx->cell, (RT *)ctx->off, (RT *)ctx->P, ctx->u_in,
+                         ctx->w, ctx->sp, ctx->id, &ctx->cnt_dev->status)));
   KCHECK();
   CK(cudaMemcpyAsync(ctx->cnt_host, ctx->cnt_dev, sizeof(EvalCounters), cudaMemcpyDeviceToHost,
                      ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   if (ctx->cnt_host->status) {
-    ctx->err = "pic_set_particles: species index out of range";
+    ctx->err = ctx->cnt_host->status & 1u ? "pic_set_particles: species index out of range"
+                                          : "pic_set_particles: node index or offset out of range";
     return PIC_EARG;
   }
   return PIC_OK;
@@ -471,17 +495,21 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
   CK(cudaMemsetAsync(ctx->cnt_dev, 0, sizeof(EvalCounters), ctx->st));
   int nb = nblk(ctx->np);
   ctx->map_final = final_pass;
+  // in the device-controlled step's graphs the map kernel times itself and
+  // the controller reads its counters on the device
+  const bool loop = ctx->loop_capture != 0;
   if (ctx->np > 0) {
     PGeom pg = pgeom(ctx);
     // inside a stream capture the records must become event nodes of the graph
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(ctx->st, &cap));
     const unsigned evf = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
-    CK(cudaEventRecordWithFlags(ctx->ev0, ctx->st, evf));
+    if (!loop) CK(cudaEventRecordWithFlags(ctx->ev0, ctx->st, evf));
+    unsigned long long *tim = loop ? ctx->map_timer : nullptr;
 #define PIC_MAP_LAUNCH(FIN, GEN)                                                          \
   PIC_DISPATCH(ctx, (k_map<DD, RT, FIN, GEN><<<nb, kPT, 0, ctx->st>>>(                      \
                          pview<RT>(ctx), (const RT *)ctx->nodes, (const RT *)ctx->nodes_u, \
-                         ctx->Jorb, pg, kconst<RT>(sc_in, pg), ctx->cnt_dev, ctx->psum)))
+                         ctx->Jorb, pg, kconst<RT>(sc_in, pg), ctx->cnt_dev, ctx->psum, tim)))
     // the general kernels (degree-one shapes, refinement) only when needed
     const bool gen = sc_in.order != 2 || sc_in.refine_max > 0;
     if (final_pass) {
@@ -493,7 +521,7 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
     }
 #undef PIC_MAP_LAUNCH
     KCHECK();
-    CK(cudaEventRecordWithFlags(ctx->ev1, ctx->st, evf));
+    if (!loop) CK(cudaEventRecordWithFlags(ctx->ev1, ctx->st, evf));
     if (ctx->opt.deterministic_deposit) {  // replaces the atomic deposit in Jorb
       int e = det_deposit(ctx, ctx->Jorb, sc_in);
       if (e) return e;
@@ -506,9 +534,22 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
                          sizeof(double) * 4 * kPsumBlocks, cudaMemcpyDeviceToHost, ctx->st));
     }
   }
-  CK(cudaMemcpyAsync(ctx->cnt_host, ctx->cnt_dev, sizeof(EvalCounters), cudaMemcpyDeviceToHost,
-                     ctx->st));
+  if (!loop)
+    CK(cudaMemcpyAsync(ctx->cnt_host, ctx->cnt_dev, sizeof(EvalCounters),
+                       cudaMemcpyDeviceToHost, ctx->st));
   return PIC_OK;
+}
+
+void particles_final_sums(const pic_ctx *ctx, double *work, double *chain) {
+  // fixed order, compensated: reproducible diagnostics
+  const double *ps = ctx->psum_host;  // kPsumBlocks (sum, error) pairs of each
+  CSum cw = csum_zero(), cc = csum_zero();
+  for (int k = 0; k < kPsumBlocks; k++) {
+    cw = csum_merge(cw, CSum{ps[4 * k], ps[4 * k + 1]});
+    cc = csum_merge(cc, CSum{ps[4 * k + 2], ps[4 * k + 3]});
+  }
+  *work = csum_value(cw);
+  *chain = csum_value(cc);
 }
 
 int particles_map_finish(pic_ctx *ctx, double *work_sum, double *chain_sum, EvalCounters *cnt) {
@@ -518,16 +559,7 @@ int particles_map_finish(pic_ctx *ctx, double *work_sum, double *chain_sum, Eval
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     ctx->map_ms += ms;
     ctx->map_launches++;
-    if (ctx->map_final) {  // fixed order, compensated: reproducible diagnostics
-      const double *ps = ctx->psum_host;  // kPsumBlocks (sum, error) pairs of each
-      CSum cw = csum_zero(), cc = csum_zero();
-      for (int k = 0; k < kPsumBlocks; k++) {
-        cw = csum_merge(cw, CSum{ps[4 * k], ps[4 * k + 1]});
-        cc = csum_merge(cc, CSum{ps[4 * k + 2], ps[4 * k + 3]});
-      }
-      work = csum_value(cw);
-      chain = csum_value(cc);
-    }
+    if (ctx->map_final) particles_final_sums(ctx, &work, &chain);
   }
   *cnt = *ctx->cnt_host;
   ctx->pushes += ctx->np;

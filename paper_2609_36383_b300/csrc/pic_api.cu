@@ -57,6 +57,7 @@ int ilog2(int n) { int l = 0; while ((1 << l) < n) l++; return l; }
 void free_all(pic_ctx *ctx) {
   tangent_free(ctx);
   det_free(ctx);
+  control_free(ctx);
   void *ptrs[] = {ctx->cell, ctx->off, ctx->P, ctx->w, ctx->sp, ctx->id, ctx->Am, ctx->v0,
                   ctx->vbar, ctx->Pnew, ctx->iters, ctx->u_in, ctx->tmp_d, ctx->tmp_i, ctx->psum,
                   ctx->phi_h, ctx->psi_h, ctx->rho_h, ctx->A_h, ctx->U_h, ctx->A_real, ctx->J_acc,
@@ -103,6 +104,8 @@ int alloc_mesh(pic_ctx *ctx) {
   CK(cudaMallocHost((void **)&ctx->cnt_host, sizeof(EvalCounters)));
   CK(cudaEventCreate(&ctx->ev0));
   CK(cudaEventCreate(&ctx->ev1));
+  int e = control_alloc(ctx);
+  if (e) return e;
   double2 *zc[] = {ctx->phi_h, ctx->psi_h, ctx->rho_h};
   for (double2 *b : zc) CK(cudaMemsetAsync(b, 0, C * Ng, ctx->st));
   CK(cudaMemsetAsync(ctx->A_h, 0, C * 3 * Ng, ctx->st));
@@ -186,6 +189,7 @@ int eval_enqueue(pic_ctx *ctx, const double *jdev, double *Hdev, double *rdev,
 void graphs_clear(pic_ctx *ctx) {
   for (int k = 0; k < ctx->ngraphs; k++) cudaGraphExecDestroy(ctx->graphs[k].exec);
   ctx->ngraphs = 0;
+  control_graphs_clear(ctx);
 }
 
 namespace {
@@ -292,6 +296,84 @@ bool solve_small(int m, double *A, double *b) {
   return true;
 }
 
+// Inexact Newton-Krylov outer iteration (option nonlinear_solver): Algorithm
+// 1's tests, backtracking and verifying evaluation, with the Newton direction
+// (I - H'(j)) d = r of nk_direction in place of the Anderson / damped Picard
+// directions.  The caller has evaluated H at the first iterate (j, H, r, T).
+int newton_krylov_outer(pic_ctx *ctx, const StepConst &sc, double tr, double ta, pic_report &R,
+                        Eval &ev, Tests &T, double *&j, double *&H, double *&r, double *&jt,
+                        double *&Ht, double *&rt, bool &done) {
+  NkState *nk = nullptr;
+  struct Release {
+    NkState **p;
+    ~Release() { nk_end(*p); }
+  } release{&nk};
+  int e = nk_begin(ctx, sc, &nk);
+  if (e) return e;
+  const size_t N3 = (size_t)3 * ctx->g.Ng;
+  int status = PIC_OK;
+  double rms_prev = 0.0, eta_prev = 0.1;
+  for (int k = 0; k < ctx->opt.outer_max; k++) {
+    TraceRange trace_k("outer_iteration");
+    R.outer_iters = k + 1;
+    R.res_scaled_rms = T.srms;
+    R.res_scaled_max = T.smax;
+    if (T.srms <= 1.0 && T.smax <= 1.0) {
+      status = eval_map(ctx, j, H, r, sc, 1, tr, ta, &ev, &T);
+      R.map_evals++;
+      if (status != PIC_OK) return status;
+      R.res_scaled_rms = T.srms;
+      R.res_scaled_max = T.smax;
+      if (!(T.srms <= 1.0 && T.smax <= 1.0)) {
+        ctx->err = "verification evaluation failed the outer tests";
+        return PIC_EOUTER;
+      }
+      done = true;
+      return PIC_OK;
+    }
+    // forcing term: Eisenstat-Walker choice 2 (gamma 0.9, exponent 2) with
+    // its safeguard, at most 0.5, and no smaller than the reduction that
+    // still brings the scaled residual to half the test's bound
+    double eta = 0.1;
+    if (k > 0) {
+      const double q = T.rms_r / rms_prev;
+      eta = 0.9 * q * q;
+      if (0.9 * eta_prev * eta_prev > 0.1) eta = std::fmax(eta, 0.9 * eta_prev * eta_prev);
+    }
+    eta = std::fmin(std::fmax(eta, 0.5 / T.srms), 0.5);
+    int its = 0;
+    e = nk_direction(ctx, nk, r, eta, ctx->dir, &its);
+    R.jvp_evals += its;
+    if (e) return e;
+    bool accepted = false;
+    Tests Tt = T;
+    double alpha = 1.0;
+    for (int lvl = 0; lvl < ctx->opt.backtrack_levels; lvl++, alpha *= 0.5) {
+      if ((e = lincomb(ctx, jt, j, 1.0, ctx->dir, alpha, N3))) return e;
+      status = eval_map(ctx, jt, Ht, rt, sc, 0, tr, ta, &ev, &Tt);
+      R.map_evals++;
+      if (status != PIC_OK) return status;
+      if (Tt.srms <= (1.0 - ctx->opt.decrease_coef * alpha) * T.srms &&
+          Tt.smax <= ctx->opt.growth_limit * T.smax) {
+        accepted = true;
+        break;
+      }
+    }
+    if (!accepted) {
+      ctx->err = "no accepted Newton step";
+      return PIC_EOUTER;
+    }
+    rms_prev = T.rms_r;
+    eta_prev = eta;
+    std::swap(j, jt);
+    std::swap(H, Ht);
+    std::swap(r, rt);
+    T = Tt;
+  }
+  ctx->err = "outer iteration limit reached";
+  return PIC_EOUTER;
+}
+
 int finish_report(pic_ctx *ctx, pic_report *R) {
   int e;
   double K, W, gr, lr;
@@ -333,6 +415,49 @@ int get_field_real(pic_ctx *ctx, const double2 *src, int ncomp, double *out, int
 int copy_in(pic_ctx *ctx, double *dst_dev, const double *src, size_t n, int on_device) {
   CK(cudaMemcpyAsync(dst_dev, src, sizeof(double) * n,
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st));
+  return PIC_OK;
+}
+
+}  // namespace
+
+namespace {
+
+int set_particles(pic_ctx *ctx, int64_t n, const int32_t *species, const int32_t *cell,
+                  const double *x, const double *u_or_P, int is_canonical, const double *w,
+                  int on_device) {
+  tangent_free(ctx);  // its arrays follow the particle storage
+  if (!ctx) return PIC_EARG;
+  if (n < 0 || (n > 0 && (!x || !u_or_P || !w))) {
+    ctx->err = "pic_set_particles: bad arguments";
+    return PIC_EARG;
+  }
+  if (species && !on_device)
+    for (int64_t i = 0; i < n; i++)
+      if (species[i] < 0 || species[i] >= ctx->nspecies) {
+        ctx->err = "pic_set_particles: species index out of range";
+        return PIC_EARG;
+      }
+  if (cell && !on_device)
+    for (int l = 0; l < ctx->g.dim; l++)
+      for (int64_t i = 0; i < n; i++)
+        if (cell[l * n + i] < 0 || cell[l * n + i] >= ctx->g.n[l] ||
+            !(x[l * n + i] >= -0.5 && x[l * n + i] < 0.5)) {
+          ctx->err = "pic_set_particles_local: node index or offset out of range";
+          return PIC_EARG;
+        }
+  graphs_clear(ctx);
+  ctx->started = 0;
+  int e = particles_alloc(ctx, n);
+  if (e) return e;
+  ctx->np = n;
+  if ((e = particles_load(ctx, species, cell, x, u_or_P, is_canonical, w, on_device))) {
+    // a refused load leaves an empty, unstarted context
+    ctx->np = 0;
+    ctx->have_particles = 0;
+    return e;
+  }
+  ctx->pending_mech = !is_canonical;
+  ctx->have_particles = 1;
   return PIC_OK;
 }
 
@@ -389,7 +514,12 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, in
       (o.precision != PIC_FP64 && o.precision != PIC_MIXED) || !(o.kappa > 0.0) ||
       !(o.sigma1 > 0.0) || !(o.sigma2 > 0.0) || (o.order != 1 && o.order != 2) ||
       o.refine_max < 0 || o.refine_max > 3 ||
-      (o.deterministic_deposit && (o.precision != PIC_FP64 || o.refine_max != 0)))
+      (o.deterministic_deposit && (o.precision != PIC_FP64 || o.refine_max != 0)) ||
+      (o.nonlinear_solver != PIC_SOLVER_ANDERSON &&
+       o.nonlinear_solver != PIC_SOLVER_NEWTON_KRYLOV) ||
+      (o.nonlinear_solver == PIC_SOLVER_NEWTON_KRYLOV &&
+       (o.precision != PIC_FP64 || o.order != 2 || o.refine_max != 0 || o.inner_warm_start ||
+        o.deterministic_deposit)))
     return PIC_EARG;
   // the deterministic deposit's node gather spans at least 5 nodes per dimension
   if (o.deterministic_deposit)
@@ -477,33 +607,19 @@ int64_t pic_num_particles(const pic_ctx *ctx) { return ctx ? ctx->np : -1; }
 
 int pic_set_particles(pic_ctx *ctx, int64_t n, const int32_t *species, const double *x,
                       const double *u_or_P, int is_canonical, const double *w, int on_device) {
-  tangent_free(ctx);  // its arrays follow the particle storage
   if (!ctx) return PIC_EARG;
-  if (n < 0 || (n > 0 && (!x || !u_or_P || !w))) {
-    ctx->err = "pic_set_particles: bad arguments";
+  return set_particles(ctx, n, species, nullptr, x, u_or_P, is_canonical, w, on_device);
+}
+
+int pic_set_particles_local(pic_ctx *ctx, int64_t n, const int32_t *species, const int32_t *cell,
+                            const double *offset, const double *u_or_P, int is_canonical,
+                            const double *w, int on_device) {
+  if (!ctx) return PIC_EARG;
+  if (n > 0 && !cell) {
+    ctx->err = "pic_set_particles_local: bad arguments";
     return PIC_EARG;
   }
-  if (species && !on_device)
-    for (int64_t i = 0; i < n; i++)
-      if (species[i] < 0 || species[i] >= ctx->nspecies) {
-        ctx->err = "pic_set_particles: species index out of range";
-        return PIC_EARG;
-      }
-  graphs_clear(ctx);
-  ctx->started = 0;
-  int e = particles_alloc(ctx, n);
-  if (e) return e;
-  ctx->np = n;
-  if ((e = particles_load(ctx, species, x, u_or_P, is_canonical, w, on_device))) {
-    // a refused load leaves an empty, unstarted context
-    ctx->np = 0;
-    ctx->have_particles = 0;
-    return e;
-  }
-  ctx->pending_mech = !is_canonical;
-  ctx->have_particles = 1;
-  ctx->started = 0;
-  return PIC_OK;
+  return set_particles(ctx, n, species, cell, offset, u_or_P, is_canonical, w, on_device);
 }
 
 int pic_set_potentials(pic_ctx *ctx, const double *A, const double *U, int on_device) {
@@ -620,15 +736,48 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
   int e;
   if ((e = particles_step_start(ctx))) return e;
   double *j = ctx->j, *H = ctx->H, *r = ctx->r, *jt = ctx->jt, *Ht = ctx->Ht, *rt = ctx->rt;
-  CK(cudaMemcpyAsync(j, ctx->J_acc, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
   Eval ev;
   Tests T;
-  int status = eval_map(ctx, j, H, r, sc, 0, tr, ta, &ev, &T);
+  int status = PIC_OK;
+  bool done = false;
+  int ran = 0;
+  const bool newton = ctx->opt.nonlinear_solver == PIC_SOLVER_NEWTON_KRYLOV;
+  if (!ctx->opt.host_control && !newton) {
+    // the whole outer iteration on the device (control.cu)
+    StepOutcome so;
+    if ((e = step_control_device(ctx, sc, tr, ta, &so, &ran))) return e;
+    if (ran) {
+      status = so.status;
+      done = status == PIC_OK;
+      R.outer_iters = so.outer_iters;
+      R.map_evals = so.map_evals;
+      R.res_scaled_rms = so.res_srms;
+      R.res_scaled_max = so.res_smax;
+      ev.work_p = so.work_p;
+      ev.chain = so.chain;
+      std::memset(&ev.cnt, 0, sizeof ev.cnt);
+      ev.cnt.inner_max = so.inner_max;
+      ev.cnt.inner_sum = so.inner_sum;
+      ev.cnt.refined = so.refined;
+      if (status == PIC_EINNER) ctx->err = "inner particle solve failed";
+      else if (status == PIC_EOUTER)
+        ctx->err = so.why == 4 ? "verification evaluation failed the outer tests"
+                   : so.why == 3 ? "no accepted outer direction"
+                                 : "outer iteration limit reached";
+    }
+  }
+  if (!ran) {
+  CK(cudaMemcpyAsync(j, ctx->J_acc, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
+  status = eval_map(ctx, j, H, r, sc, 0, tr, ta, &ev, &T);
   R.map_evals = 1;
   if (status != PIC_OK && status != PIC_EINNER) return status;
+  if (newton && status == PIC_OK) {
+    status = newton_krylov_outer(ctx, sc, tr, ta, R, ev, T, j, H, r, jt, Ht, rt, done);
+    if (status != PIC_OK && status != PIC_EINNER && status != PIC_EOUTER) return status;
+  }
+  if (!newton) {
   // Anderson history: ring of M columns, oldest at hist0
   int mh = 0, hist0 = 0;
-  bool done = false;
   for (int k = 0; status == PIC_OK && k < ctx->opt.outer_max; k++) {
     TraceRange trace_k("outer_iteration");
     R.outer_iters = k + 1;
@@ -650,7 +799,7 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
       break;
     }
     bool have_anderson = false;
-    if (k >= ctx->opt.anderson_start && mh > 0) {
+    if (k + 1 >= ctx->opt.anderson_start && mh > 0) {  // iterations counted from 1
       const double *cols[PIC_MAX_ANDERSON], *jcols[PIC_MAX_ANDERSON];
       for (int c = 0; c < mh; c++) {
         int slot = (hist0 + c) % M;
@@ -712,7 +861,8 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
       }
       if ((e = diff_into(ctx, ctx->dJ + (size_t)slot * N3, jt, j, N3))) return e;
       if ((e = diff_into(ctx, ctx->dR + (size_t)slot * N3, rt, r, N3))) return e;
-      if (Tt.rms_r > ctx->opt.growth_limit * T.rms_r) { mh = 0; hist0 = 0; }
+      const double grown = ctx->opt.growth_scaled ? Tt.srms / T.srms : Tt.rms_r / T.rms_r;
+      if (grown > ctx->opt.growth_limit) { mh = 0; hist0 = 0; }
     }
     std::swap(j, jt);
     std::swap(H, Ht);
@@ -723,6 +873,8 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
     status = PIC_EOUTER;
     ctx->err = "outer iteration limit reached";
   }
+  }  // Anderson
+  }  // host-driven outer iteration
   // the forward sensitivity of the converged step (before anything commits)
   if (status == PIC_OK && ctx->tan) {
     status = tangent_solve(ctx, sc, tol);

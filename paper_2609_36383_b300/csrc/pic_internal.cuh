@@ -115,7 +115,7 @@ struct pic_ctx {
   int32_t *cnt_sort;  // [Ng] per-cell counts / cursors of the sort
   void *tmp_r;        // [3][cap] scratch of particle reals
   double *tmp_d;      // [3][cap]
-  int32_t *tmp_i;     // [3][cap]
+  int32_t *tmp_i;     // [4][cap]: staged species, then staged node indices
   int64_t *tmp_l;
 
   // ---- mesh: accepted state (spectral primary + real copies) ------------
@@ -146,6 +146,21 @@ struct pic_ctx {
   double *psum;       // per-block particle sums (work, chain, K)
   double *psum_host;  // pinned copy of the final-pass partials
   int map_final;      // the queued particle map is a final (diagnostic) pass
+  // ---- device-controlled step (control.cu) ------------------------------
+  int loop_capture;              // capturing the controlled step's graphs
+  unsigned long long *map_timer; // [2] first start, last end of the map launch (ns)
+  struct SCtl *sctl;             // controller state (device)
+  struct SCtl *sctl_host;        // pinned copy read after the step
+  double *sred;                  // block partials of the residual and Gram sums
+  struct StepGraphs {
+    const void *phi, *A;
+    double tr, ta, itr, ita;
+    int64_t np;
+    cudaGraphExec_t loop, verify;
+    int nk_round, nk_verify;  // kernels per loop round, in the verification
+  } sgraphs[4];
+  int nsgraphs;
+  int sgraphs_off;               // the graphs could not be built: the host drives the step
   // ---- statistics (pic_stats) ------------------------------------------
   long long launches;          // kernels launched by this context
   long long map_launches;      // particle-map kernel launches
@@ -263,8 +278,8 @@ int field_mesh_work_real(pic_ctx *ctx, const double *H, double *work);
 
 // ---------------------------------------------------------------- particle.cu
 int particles_alloc(pic_ctx *ctx, int64_t n);
-int particles_load(pic_ctx *ctx, const int32_t *sp, const double *x, const double *uP,
-                   int canonical, const double *w, int on_device);
+int particles_load(pic_ctx *ctx, const int32_t *sp, const int32_t *cell_in, const double *x,
+                   const double *uP, int canonical, const double *w, int on_device);
 int particles_form_P(pic_ctx *ctx);
 int particles_point_deposit(pic_ctx *ctx, double *rho, double *J);
 int particles_step_start(pic_ctx *ctx);
@@ -272,6 +287,8 @@ int particles_step_start(pic_ctx *ctx);
 // host memory; particles_map_finish reads them after the stream is synced
 int particles_map_launch(pic_ctx *ctx, const StepConst &sc, int final_pass);
 int particles_map_finish(pic_ctx *ctx, double *work_sum, double *chain_sum, EvalCounters *cnt);
+// the final pass's work and chain-rule sums from the pinned partials
+void particles_final_sums(const pic_ctx *ctx, double *work, double *chain);
 int particles_commit(pic_ctx *ctx);
 int particles_kinetic(pic_ctx *ctx, double *K);
 // refresh the particle-precision copy of A^n after A_real changed
@@ -301,6 +318,30 @@ int det_sort_slots(pic_ctx *ctx, int64_t *slot);
 int tangent_solve(pic_ctx *ctx, const StepConst &sc, double tol);
 int tangent_commit(pic_ctx *ctx);
 void tangent_free(pic_ctx *ctx);
+// Newton-Krylov outer solver: scratch for the step (dual particle inputs at
+// the step start), the inexact Newton direction (I - H'(j)) x = r by
+// GMRES to relative residual eta (*iters: tangent map evaluations), release
+struct NkState;
+int nk_begin(pic_ctx *ctx, const StepConst &sc, NkState **out);
+int nk_direction(pic_ctx *ctx, NkState *nk, const double *r, double eta, double *x, int *iters);
+void nk_end(NkState *nk);
+
+// ---------------------------------------------------------------- control.cu
+// Algorithm 1's outer iteration decided on the device (one context)
+struct StepOutcome {
+  int status, why, outer_iters, map_evals, inner_max;
+  unsigned long long inner_sum, refined;  // of the final (verification) evaluation
+  double res_srms, res_smax, work_p, chain;
+};
+int control_alloc(pic_ctx *ctx);
+void control_free(pic_ctx *ctx);
+void control_graphs_clear(pic_ctx *ctx);
+// Runs the outer iteration of one step from the accepted current J_acc with
+// the graphs of control.cu; *ran = 0 when they cannot be used (the caller
+// then drives the step from the host).  On success of the step ctx->j holds
+// the accepted current, ctx->H its map value from the final evaluation.
+int step_control_device(pic_ctx *ctx, const StepConst &sc, double tr, double ta, StepOutcome *out,
+                        int *ran);
 
 // ---------------------------------------------------------------- reduce.cu
 // queue r = H - j and its test sums (copied to pinned host memory);

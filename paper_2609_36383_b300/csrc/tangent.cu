@@ -215,13 +215,13 @@ int launch_dual_map(pic_ctx *ctx, const PView<Dual> &pv, const Dual *rec, double
   const int nb = nblk(pv.np);
   if (ctx->g.dim == 1)
     k_map<1, Dual, false, false><<<nb, kPT, 0, ctx->st>>>(pv, rec, rec, Jd, pg, kc, ctx->cnt_dev,
-                                                          ctx->psum);
+                                                          ctx->psum, nullptr);
   else if (ctx->g.dim == 2)
     k_map<2, Dual, false, false><<<nb, kPT, 0, ctx->st>>>(pv, rec, rec, Jd, pg, kc, ctx->cnt_dev,
-                                                          ctx->psum);
+                                                          ctx->psum, nullptr);
   else
     k_map<3, Dual, false, false><<<nb, kPT, 0, ctx->st>>>(pv, rec, rec, Jd, pg, kc, ctx->cnt_dev,
-                                                          ctx->psum);
+                                                          ctx->psum, nullptr);
   KCHECK();
   return PIC_OK;
 }
@@ -363,7 +363,9 @@ void tangent_free(pic_ctx *ctx) {
 
 namespace {
 
-int tangent_alloc(pic_ctx *ctx) {
+// A tangent state with its scratch, all zero (a zero state tangent), not
+// attached to the context; null (ctx->err set) if the allocation fails.
+TangentState *tangent_state_new(pic_ctx *ctx) {
   const size_t d = ctx->g.dim, Ng = ctx->g.Ng, nvp = node_record_len((int)d);
   const size_t cap = ctx->cap, N3 = 3 * Ng;
   const size_t C = sizeof(double2), R = sizeof(double), Q = sizeof(Dual);
@@ -380,13 +382,11 @@ int tangent_alloc(pic_ctx *ctx) {
   const int np_ = (int)(sizeof parts / sizeof parts[0]);
   for (int k = 0; k < np_; k++) off[k + 1] = off[k] + (parts[k] + 255) / 256 * 256;
   TangentState *t = new TangentState();
-  ctx->tan = t;
   if (cudaMalloc(&t->block, off[np_]) != cudaSuccess) {
     cudaGetLastError();
-    t->block = nullptr;
-    tangent_free(ctx);
-    ctx->err = "pic_tangent_begin: device allocation failed";
-    return PIC_ENOMEM;
+    delete t;
+    ctx->err = "tangent state: device allocation failed";
+    return nullptr;
   }
   char *b = (char *)t->block;
   t->off = (double *)(b + off[0]);
@@ -408,7 +408,26 @@ int tangent_alloc(pic_ctx *ctx) {
   t->w = (double *)(b + off[15]);
   t->Tx = (double *)(b + off[16]);
   t->gmres_iters = 0;
-  CK(cudaMemsetAsync(t->block, 0, off[np_], ctx->st));
+  if (cudaMemsetAsync(t->block, 0, off[np_], ctx->st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(t->block);
+    delete t;
+    ctx->err = "tangent state: clearing failed";
+    return nullptr;
+  }
+  return t;
+}
+
+void tangent_state_delete(TangentState *t) {
+  if (!t) return;
+  if (t->block) cudaFree(t->block);
+  delete t;
+}
+
+int tangent_alloc(pic_ctx *ctx) {
+  TangentState *t = tangent_state_new(ctx);
+  if (!t) return PIC_ENOMEM;
+  ctx->tan = t;
   return PIC_OK;
 }
 
@@ -416,9 +435,8 @@ int tangent_alloc(pic_ctx *ctx) {
 // primal in ctx->nodes): out = P dJ_orb for the tangent trial current v and
 // the state tangent; the tangent candidates f1, A1_real and the dual vbar,
 // Pnew of the particles are those of v afterwards.
-int tangent_eval(pic_ctx *ctx, const PView<Dual> &pv, const KConst<Dual> &kc, const double *v,
-                 double *out) {
-  TangentState &t = *ctx->tan;
+int tangent_eval(pic_ctx *ctx, TangentState &t, const PView<Dual> &pv, const KConst<Dual> &kc,
+                 const double *v, double *out) {
   const int Ng = ctx->g.Ng, nvp = node_record_len(ctx->g.dim);
   const size_t N3 = (size_t)3 * Ng;
   int e;
@@ -473,7 +491,7 @@ int tangent_solve(pic_ctx *ctx, const StepConst &sc, double tol) {
   const double rtol = std::fmax(tol, 1e-12);
   t.gmres_iters = 0;
   CK(cudaMemsetAsync(t.x, 0, sizeof(double) * N3, ctx->st));
-  if ((e = tangent_eval(ctx, pv, kc, t.x, t.b))) return e;  // b = T(0)
+  if ((e = tangent_eval(ctx, t, pv, kc, t.x, t.b))) return e;  // b = T(0)
   const double bn = norm2(ctx, t.b, &e);
   if (e) return e;
   if (!std::isfinite(bn)) {
@@ -496,7 +514,7 @@ int tangent_solve(pic_ctx *ctx, const StepConst &sc, double tol) {
     for (int k = 0; k < m; k++) {
       double *Vk = t.V + (size_t)k * N3, *Vn = t.V + (size_t)(k + 1) * N3;
       // w = V_k - T(V_k) + b
-      if ((e = tangent_eval(ctx, pv, kc, Vk, t.w))) return e;
+      if ((e = tangent_eval(ctx, t, pv, kc, Vk, t.w))) return e;
       if ((e = lincomb(ctx, t.w, Vk, 1.0, t.w, -1.0, N3))) return e;
       if ((e = lincomb(ctx, t.w, t.w, 1.0, t.b, 1.0, N3))) return e;
       t.gmres_iters++;
@@ -549,7 +567,7 @@ int tangent_solve(pic_ctx *ctx, const StepConst &sc, double tol) {
       if ((e = lincomb(ctx, t.x, t.x, 1.0, t.V + (size_t)i * N3, y[i], N3))) return e;
     // true residual r = T(x) - x into V_0, measured against the larger of
     // |b| and |x| (the solution may be larger than the right-hand side)
-    if ((e = tangent_eval(ctx, pv, kc, t.x, t.Tx))) return e;
+    if ((e = tangent_eval(ctx, t, pv, kc, t.x, t.Tx))) return e;
     if ((e = lincomb(ctx, V0, t.Tx, 1.0, t.x, -1.0, N3))) return e;
     beta = norm2(ctx, V0, &e);
     if (e) return e;
@@ -566,6 +584,135 @@ int tangent_solve(pic_ctx *ctx, const StepConst &sc, double tol) {
   ctx->err = "tangent step: GMRES did not reach the tolerance (relative residuals " + hist +
              ")";
   return PIC_EOUTER;
+}
+
+// ---------------------------------------------------------- Newton-Krylov
+// The Newton direction of the outer equation H(j) - j = 0 at the current
+// iterate, for the Newton-Krylov alternative to Algorithm 1's Anderson
+// iteration: (I - H'(j)) delta = r by GMRES(kKrylov) with up to two
+// restarts, to the relative residual eta (an inexact Newton step).  H'(j) v
+// is the tangent map with a zero state tangent: one dual map evaluation at
+// the gather records of the last plain evaluation (those of j).
+struct NkState {
+  TangentState *t;
+  PView<Dual> pv;
+  KConst<Dual> kc;
+};
+
+int nk_begin(pic_ctx *ctx, const StepConst &sc, NkState **out) {
+  *out = nullptr;
+  TangentState *t = tangent_state_new(ctx);
+  if (!t) return PIC_ENOMEM;
+  NkState *nk = new NkState();
+  nk->t = t;
+  nk->kc = kconst<Dual>(sc, pgeom(ctx));
+  nk->pv = dual_view(ctx, (Dual *)t->dpart);
+  *out = nk;
+  int e;
+  if (ctx->np > 0) {  // the particle inputs with zero tangents, and the dual step start
+    Dual *off_d = const_cast<Dual *>(nk->pv.off), *P_d = const_cast<Dual *>(nk->pv.P);
+    k_zip<<<grid1(ctx->np), 256, 0, ctx->st>>>((const double *)ctx->off, nullptr, off_d, ctx->np,
+                                               ctx->g.dim, ctx->cap, ctx->cap);
+    KCHECK();
+    k_zip<<<grid1(ctx->np), 256, 0, ctx->st>>>((const double *)ctx->P, nullptr, P_d, ctx->np, 3,
+                                               ctx->cap, ctx->cap);
+    KCHECK();
+    if ((e = launch_dual_step_start(ctx, nk->pv, nullptr, nk->kc))) return e;
+  }
+  return PIC_OK;
+}
+
+void nk_end(NkState *nk) {
+  if (!nk) return;
+  tangent_state_delete(nk->t);
+  delete nk;
+}
+
+int nk_direction(pic_ctx *ctx, NkState *nk, const double *r, double eta, double *x, int *iters) {
+  TraceRange trace("newton_direction");
+  TangentState &t = *nk->t;
+  const size_t N3 = (size_t)3 * ctx->g.Ng;
+  const int m = kKrylov;
+  int e;
+  *iters = 0;
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * N3, ctx->st));
+  double *V0 = t.V;
+  CK(cudaMemcpyAsync(V0, r, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
+  double beta = norm2(ctx, V0, &e);
+  if (e) return e;
+  const double ref = beta;
+  if (!(beta > 0.0)) return PIC_OK;
+  for (int restart = 0; restart < 3; restart++) {
+    if ((e = lincomb(ctx, V0, V0, 1.0 / beta, V0, 0.0, N3))) return e;
+    std::vector<double> H((m + 1) * m, 0.0), g(m + 1, 0.0), cs(m, 0.0), sn(m, 0.0);
+    g[0] = beta;
+    int kk = 0;
+    for (int k = 0; k < m; k++) {
+      double *Vk = t.V + (size_t)k * N3, *Vn = t.V + (size_t)(k + 1) * N3;
+      // w = V_k - H'(j) V_k
+      if ((e = tangent_eval(ctx, t, nk->pv, nk->kc, Vk, t.w))) return e;
+      if ((e = lincomb(ctx, t.w, Vk, 1.0, t.w, -1.0, N3))) return e;
+      (*iters)++;
+      for (int pass = 0; pass < 2; pass++) {
+        const double *pa[kKrylov + 1], *pb[kKrylov + 1];
+        double h[kKrylov + 1];
+        for (int i = 0; i <= k; i++) {
+          pa[i] = t.V + (size_t)i * N3;
+          pb[i] = t.w;
+        }
+        if ((e = dots(ctx, pa, pb, k + 1, h))) return e;
+        for (int i = 0; i <= k; i++) {
+          H[i * m + k] += h[i];
+          if ((e = lincomb(ctx, t.w, t.w, 1.0, pa[i], -h[i], N3))) return e;
+        }
+      }
+      const double hn = norm2(ctx, t.w, &e);
+      if (e) return e;
+      if (!std::isfinite(hn)) {
+        ctx->err = "Newton direction: non-finite Krylov vector";
+        return PIC_EOUTER;
+      }
+      H[(k + 1) * m + k] = hn;
+      for (int i = 0; i < k; i++) {
+        const double a = H[i * m + k], c = H[(i + 1) * m + k];
+        H[i * m + k] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * m + k] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[k * m + k], c = H[(k + 1) * m + k];
+      const double rr = std::hypot(a, c);
+      cs[k] = rr > 0.0 ? a / rr : 1.0;
+      sn[k] = rr > 0.0 ? c / rr : 0.0;
+      H[k * m + k] = rr;
+      H[(k + 1) * m + k] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      kk = k + 1;
+      if (hn > 0.0 && (e = lincomb(ctx, Vn, t.w, 1.0 / hn, t.w, 0.0, N3))) return e;
+      if (std::fabs(g[k + 1]) <= eta * ref || hn == 0.0) break;
+    }
+    std::vector<double> y(kk, 0.0);
+    for (int i = kk - 1; i >= 0; i--) {
+      double s = g[i];
+      for (int q = i + 1; q < kk; q++) s -= H[i * m + q] * y[q];
+      y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
+    }
+    for (int i = 0; i < kk; i++)
+      if ((e = lincomb(ctx, x, x, 1.0, t.V + (size_t)i * N3, y[i], N3))) return e;
+    if (std::fabs(g[kk]) <= eta * ref) return PIC_OK;
+    // restart from the true residual r - (x - H'(j) x)
+    if ((e = tangent_eval(ctx, t, nk->pv, nk->kc, x, t.Tx))) return e;
+    (*iters)++;
+    if ((e = lincomb(ctx, V0, r, 1.0, x, -1.0, N3))) return e;
+    if ((e = lincomb(ctx, V0, V0, 1.0, t.Tx, 1.0, N3))) return e;
+    beta = norm2(ctx, V0, &e);
+    if (e) return e;
+    if (!std::isfinite(beta)) {
+      ctx->err = "Newton direction: non-finite residual";
+      return PIC_EOUTER;
+    }
+    if (beta <= eta * ref) return PIC_OK;
+  }
+  return PIC_OK;  // an inexact direction; the backtracking decides
 }
 
 int tangent_commit(pic_ctx *ctx) {

@@ -19,6 +19,7 @@ tangent to about 1e-7 of its size; the bound is 2e-6.
 import numpy as np
 import pytest
 
+import paper_2609_36383_b300 as pic
 import pic_inputs
 from tests._common import gross_scales, make_gpu, make_oracle, small_1d, small_2d
 
@@ -214,3 +215,41 @@ def test_newton_krylov_outer_solve_reaches_the_step_fixed_point():
     print(f"Newton-Krylov: {newton} Newton steps, {evals} map evaluations (with tangents); "
           f"Picard/Anderson: {r['map_evals']} map evaluations; |j - J| = {err:.2e}")
     assert err < 1e-7
+
+
+@pytest.mark.parametrize("make_cfg,tol", [(small_1d, 1e-12), (small_2d, 1e-10)], ids=["1d", "2d"])
+def test_newton_krylov_option_matches_algorithm_1(make_cfg, tol):
+    """The library's Newton-Krylov outer solver (nonlinear_solver =
+    PIC_SOLVER_NEWTON_KRYLOV) against Algorithm 1's Anderson iteration over
+    three steps from the same state: every step passes the same outer tests
+    and verification, so the committed states agree to the outer tolerance
+    and the energy theorem holds on both; the evaluation counts are
+    reported (plain map evaluations and Jacobian-vector products)."""
+    cfg = make_cfg()
+    a = make_gpu(cfg)
+    n = make_gpu(cfg, nonlinear_solver=pic.PIC_SOLVER_NEWTON_KRYLOV)
+    a.start()
+    n.start()
+    for st in range(3):
+        ra, rn = a.step(tol), n.step(tol)
+        assert ra["status"] == 0 and rn["status"] == 0, rn
+        assert rn["jvp_evals"] > 0 and ra["jvp_evals"] == 0
+        assert rn["res_scaled_rms"] <= 1.0 and rn["res_scaled_max"] <= 1.0
+        assert abs(rn["rel_dE"]) < 1e-11 and rn["chain_rms"] < 1e-13
+        print(f"step {st}: Anderson {ra['outer_iters']} iterations / {ra['map_evals']} evaluations;"
+              f" Newton-Krylov {rn['outer_iters']} iterations / {rn['map_evals']} evaluations + "
+              f"{rn['jvp_evals']} JVPs")
+    Ja, Jn = a.fields()["J"], n.fields()["J"]
+    assert np.abs(Jn - Ja).max() <= 1e-8 * np.abs(Ja).max()
+    xa, Pa, _, _ = a.particles()
+    xn, Pn, _, _ = n.particles()
+    assert np.abs(Pn - Pa).max() <= 1e-9 * np.abs(Pa).max()
+    a.close()
+    n.close()
+
+
+def test_newton_krylov_option_is_refused_where_the_tangent_is_not_built():
+    for kw in (dict(precision=pic.PIC_MIXED), dict(order=1), dict(refine_max=1),
+               dict(inner_warm_start=1)):
+        with pytest.raises(pic.PicError):
+            make_gpu(small_1d(), nonlinear_solver=pic.PIC_SOLVER_NEWTON_KRYLOV, **kw)

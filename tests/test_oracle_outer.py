@@ -8,7 +8,7 @@ affine maps H(j) = M j + b, for which the mathematics fixes what it must do:
   hand on a two-node vector (a dropped 1/2, an RMS over nodes instead of
   components, or a per-component instead of per-node norm all change them);
 - damped Picard j + beta r before the iteration where Anderson becomes
-  eligible;
+  eligible (iterations counted from 1, so m_A = 2 leaves one Picard step);
 - type-II Anderson with an untruncated history is GMRES in disguise (Walker
   and Ni, SIAM J. Numer. Anal. 49 (2011) 1715): the averaged iterate
   xbar_k = j_k - dJ gamma minimises |r| over the affine hull of the iterates
@@ -80,19 +80,25 @@ def test_picard_before_anderson_becomes_eligible(orc):
                                       lambda_=0.0, **_PLAIN)
     assert st == 0
     beta = 0.5
-    for k in (0, 1):  # iterations 0 and 1 are damped Picard with alpha = 1
-        assert tr["kind"][k] == 0 and tr["alpha"][k] == 1.0
-        r = M @ tr["j"][k] + b - tr["j"][k]
-        np.testing.assert_allclose(tr["j"][k + 1], tr["j"][k] + beta * r, rtol=0, atol=1e-14)
-    assert (tr["kind"][2:-1] == 1).all()  # then Anderson on every iteration
+    # iterations are counted from 1 and m_A = 2: the first is damped Picard
+    # with alpha = 1, every later one Anderson
+    assert tr["kind"][0] == 0 and tr["alpha"][0] == 1.0
+    r = M @ tr["j"][0] + b - tr["j"][0]
+    np.testing.assert_allclose(tr["j"][1], tr["j"][0] + beta * r, rtol=0, atol=1e-14)
+    assert (tr["kind"][1:-1] == 1).all()
+    # with m_A = 3 the first two are damped Picard
+    st, _, rep, tr = orc.outer_affine(M, b, np.zeros(6), trace_cap=40, anderson_m=8,
+                                      anderson_start=3, lambda_=0.0, **_PLAIN)
+    assert st == 0
+    assert (tr["kind"][:2] == 0).all() and (tr["kind"][2:-1] == 1).all()
 
 
 def test_anderson_untruncated_is_gmres(orc):
     """Iterates against GMRES (Walker and Ni 2011); convergence once the Krylov
-    space is the whole 6-dimensional space: Anderson at iteration 6 has six
-    columns, so xbar_6 is the solution, j_7 = xbar_6 + beta r(xbar_6) too,
-    and the tests pass at iteration 7 (outer_iters = dim + 2, the first two
-    iterations being damped Picard)."""
+    space is the whole 6-dimensional space: the Anderson step of 0-based
+    iteration 6 has six columns, so xbar_6 is the solution, j_7 = xbar_6 +
+    beta r(xbar_6) too, and the tests pass at 0-based iteration 7
+    (outer_iters = dim + 2)."""
     n3 = 6
     M, b = _affine(2, n3, -0.5, 0.9)
     j0 = np.zeros(n3)
@@ -105,7 +111,7 @@ def test_anderson_untruncated_is_gmres(orc):
     beta = 0.5
     Bmat = (1 - beta) * np.eye(n3) + beta * M  # j_{k+1} = Bmat xbar_k + beta b when alpha = 1
     checked = 0
-    for k in range(2, tr["kind"].size):
+    for k in range(1, tr["kind"].size):
         if tr["kind"][k] != 1 or tr["alpha"][k] != 1.0 or k >= n3:
             continue
         xbar = np.linalg.solve(Bmat, tr["j"][k + 1] - beta * b)
