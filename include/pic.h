@@ -139,6 +139,16 @@ typedef struct {
                                    refinement, the cold inner start and the atomic deposit
                                    (pic_init returns PIC_EARG otherwise); the host drives
                                    the iteration */
+  int fp32_first;               /* 1: each step's outer iteration first runs with the
+                                   particle map in FP32 arithmetic (the particle state
+                                   stays FP64), to max(tol, mixed_tol_floor) and without
+                                   verification, then continues in FP64 from that current
+                                   to tol, verifies and commits as an FP64 step: FP64
+                                   results (energy conserved to the FP64 tolerance) from
+                                   fewer FP64 map evaluations.  FP64 contexts with
+                                   quadratic shapes, no refinement, the Anderson solver,
+                                   device control and the atomic deposit (pic_init
+                                   returns PIC_EARG otherwise); default 0 */
 } pic_options;
 
 #define PIC_SOLVER_ANDERSON 0
@@ -159,6 +169,9 @@ typedef struct {
                                    substeps (refine_max > 0) */
   int jvp_evals;                /* Jacobian-vector products (dual-number map
                                    evaluations) of the Newton-Krylov solver; 0 otherwise */
+  int fp32_evals;               /* map evaluations of the FP32 stage (option fp32_first),
+                                   included in map_evals; its iterations are included
+                                   in outer_iters */
 } pic_report;
 
 /* Fill *opt with the paper's defaults (see pic_options). */

@@ -57,6 +57,7 @@ class Options(C.Structure):
         ("sort_every", C.c_int), ("cuda_stream", C.c_void_p), ("inner_warm_start", C.c_int),
         ("order", C.c_int), ("refine_max", C.c_int), ("deterministic_deposit", C.c_int),
         ("growth_scaled", C.c_int), ("host_control", C.c_int), ("nonlinear_solver", C.c_int),
+        ("fp32_first", C.c_int),
     ]
 
 
@@ -101,7 +102,7 @@ class Report(C.Structure):
         ("chain_rms", C.c_double), ("res_scaled_rms", C.c_double), ("res_scaled_max", C.c_double),
         ("outer_iters", C.c_int), ("map_evals", C.c_int), ("inner_max", C.c_int),
         ("inner_mean", C.c_double), ("status", C.c_int), ("refined", C.c_int),
-        ("jvp_evals", C.c_int),
+        ("jvp_evals", C.c_int), ("fp32_evals", C.c_int),
     ]
 
     def as_dict(self) -> dict:

@@ -402,12 +402,14 @@ __global__ void k_saccept(double *__restrict__ j, double *__restrict__ H, double
   }
 }
 
-// step start: j = the accepted current, controller reset
+// step start: j = the accepted current (Jacc null: j is kept, a second
+// stage continues from the first one's iterate), controller reset
 __global__ void k_sinit(double *__restrict__ j, const double *__restrict__ Jacc, size_t N3,
                         SCtl *__restrict__ ctl, unsigned long long *__restrict__ tim) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N3;
-       i += (size_t)gridDim.x * blockDim.x)
-    j[i] = Jacc[i];
+  if (Jacc)
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N3;
+         i += (size_t)gridDim.x * blockDim.x)
+      j[i] = Jacc[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     SCtl &s = *ctl;
     s.stage = SC_START;
@@ -616,14 +618,14 @@ void control_free(pic_ctx *ctx) {
 }
 
 int step_control_device(pic_ctx *ctx, const StepConst &sc, double tr, double ta, StepOutcome *out,
-                        int *ran) {
+                        int *ran, int from_j, int verify) {
   *ran = 0;
   if (ctx->sgraphs_off || ctx->graphs_off || ctx->np == 0 || !ctx->sctl) return PIC_OK;
   pic_ctx::StepGraphs *ent = nullptr;
   for (int k = 0; k < ctx->nsgraphs; k++) {
     pic_ctx::StepGraphs &g = ctx->sgraphs[k];
     if (g.phi == ctx->phi_h && g.A == ctx->A_real && g.tr == tr && g.ta == ta &&
-        g.itr == sc.tau_r && g.ita == sc.tau_a && g.np == ctx->np) {
+        g.itr == sc.tau_r && g.ita == sc.tau_a && g.np == ctx->np && g.f32 == ctx->eval_f32) {
       ent = &g;
       break;
     }
@@ -642,27 +644,30 @@ int step_control_device(pic_ctx *ctx, const StepConst &sc, double tr, double ta,
     g.itr = sc.tau_r;
     g.ita = sc.tau_a;
     g.np = ctx->np;
+    g.f32 = ctx->eval_f32;
     ctx->nsgraphs++;
     ent = &g;
   }
   *ran = 1;
   const size_t N3 = 3 * (size_t)ctx->g.Ng;
-  k_sinit<<<sgrid(N3), kST, 0, ctx->st>>>(ctx->j, ctx->J_acc, N3, ctx->sctl, ctx->map_timer);
+  k_sinit<<<sgrid(N3), kST, 0, ctx->st>>>(ctx->j, from_j ? nullptr : ctx->J_acc, N3, ctx->sctl,
+                                          ctx->map_timer);
   KCHECK();
   CK(cudaGraphLaunch(ent->loop, ctx->st));
-  CK(cudaGraphLaunch(ent->verify, ctx->st));
+  if (verify) CK(cudaGraphLaunch(ent->verify, ctx->st));
   CK(cudaMemcpyAsync(ctx->sctl_host, ctx->sctl, sizeof(SCtl), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   const SCtl &s = *ctx->sctl_host;
   const bool verified = s.verify_ran != 0;
   const int loop_rounds = s.rounds - (verified ? 1 : 0);
-  ctx->launches += (long long)ent->nk_round * loop_rounds + (verified ? ent->nk_verify : 1);
+  ctx->launches += (long long)ent->nk_round * loop_rounds + (verified ? ent->nk_verify : verify);
   ctx->map_launches += s.map_evals;
   ctx->map_ms += 1e-6 * (double)s.map_ns;
   ctx->pushes += (long long)ctx->np * s.map_evals;
   ctx->inner_iters += (long long)s.inner_sum;
   ctx->pieces += (long long)s.pieces;
   ctx->refined += (long long)s.refined;
+  out->converged = s.stage == SC_VERIFY || s.stage == SC_DONE;  // the tests passed
   out->status = s.stage == SC_DONE ? PIC_OK : s.status;
   out->why = s.why;
   out->outer_iters = s.outer_iters;

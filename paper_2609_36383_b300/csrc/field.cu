@@ -552,7 +552,11 @@ int field_pack_nodes(pic_ctx *ctx, int want_uhalf) {
   int st = fft_nd(ctx, ctx->work_h, nc, +1);
   if (st) return st;
   double inv = 1.0 / Ng;
-  if (ctx->rsize == 8)
+  if (ctx->eval_f32)  // FP32 records for the FP32 stage of an FP64 context
+    k_pack_nodes<float><<<blocks(Ng), kThreads, 0, ctx->st>>>(
+        ctx->work_h, ctx->A_real, ctx->A1_real, ctx->nodes_f, ctx->nodes_u_f, Ng, d,
+        node_record_len(d), inv, want_uhalf);
+  else if (ctx->rsize == 8)
     k_pack_nodes<double><<<blocks(Ng), kThreads, 0, ctx->st>>>(
         ctx->work_h, ctx->A_real, ctx->A1_real, (double *)ctx->nodes, (double *)ctx->nodes_u, Ng,
         d, node_record_len(d), inv, want_uhalf);

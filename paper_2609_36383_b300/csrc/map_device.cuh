@@ -1179,8 +1179,8 @@ __device__ __noinline__ bool refine_particle(const PushConst<T> &pc0, const int 
 // refinement; GEN = true reads the shape degree from kc and compiles in the
 // refinement retry (kc.refine_max > 0).  Keeping both out of the common
 // path leaves it with no call and no per-point branch on the degree.
-template <int D, typename T, bool FINAL, bool GEN = false>
-__device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i_slot,
+template <int D, typename T, bool FINAL, bool GEN = false, typename S = T>
+__device__ __forceinline__ void map_block(const PView<S> &pv, const int64_t i_slot,
                                           const T *__restrict__ nodes,
                                           const T *__restrict__ nodes_u, double *__restrict__ J,
                                           const PGeom &pg, const KConst<T> &kc,
@@ -1202,8 +1202,8 @@ __device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i_sl
       cls = 0;
 #pragma unroll
       for (int l = 0; l < D; l++) {
-        const T u = pv.off[l * pv.cap + i_slot] +
-                    (kc.warm ? pv.vbar[l * pv.cap + i_slot] : pv.v0[l * pv.cap + i_slot]) *
+        const T u = (T)pv.off[l * pv.cap + i_slot] +
+                    (T)(kc.warm ? pv.vbar[l * pv.cap + i_slot] : pv.v0[l * pv.cap + i_slot]) *
                         kc.dt * ms.inv_dx[l];
         cls += (u >= T(0.5) || u < T(-0.5)) ? 1 : 0;
       }
@@ -1263,16 +1263,16 @@ __device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i_sl
 #pragma unroll
     for (int l = 0; l < D; l++) {
       cell[l] = pv.cell[l * cap + i];
-      off[l] = pv.off[l * cap + i];
+      off[l] = (T)pv.off[l * cap + i];
       dtdx[l] = dt * ms.inv_dx[l];
     }
     T vb[3], Pn1[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      pc.Pn[c] = pv.P[c * cap + i];
-      pc.Am[c] = pv.Am[c * cap + i];
+      pc.Pn[c] = (T)pv.P[c * cap + i];
+      pc.Am[c] = (T)pv.Am[c * cap + i];
       pc.pn[c] = pc.Pn[c] - pc.q * pc.Am[c];
-      vb[c] = kc.warm ? pv.vbar[c * cap + i] : pv.v0[c * cap + i];
+      vb[c] = (T)(kc.warm ? pv.vbar[c * cap + i] : pv.v0[c * cap + i]);
       Pn1[c] = pc.Pn[c];
     }
     pc.gamma_n = sqrt(T(1) + (pc.pn[0] * pc.pn[0] + pc.pn[1] * pc.pn[1] + pc.pn[2] * pc.pn[2]) *
@@ -1306,8 +1306,8 @@ __device__ __forceinline__ void map_block(const PView<T> &pv, const int64_t i_sl
     st |= st0;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      pv.vbar[c * cap + i] = vb[c];
-      pv.Pnew[c * cap + i] = Pn1[c];
+      pv.vbar[c * cap + i] = (S)vb[c];
+      pv.Pnew[c * cap + i] = (S)Pn1[c];
     }
     pv.iters[i] = iters;
   }
@@ -1357,18 +1357,20 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // FP32 instances: at least 4 resident CTAs (<= 128 registers) to hide latency;
 // FP64 instances are bound by the FP64 pipe and keep their registers.
+// S is the particle storage type: T itself, or double under FP32 arithmetic
+// (the FP32 stage of an FP64 context, option fp32_first).
 // tim (may be null): the launch's first CTA start and last CTA end on the
 // global nanosecond timer, folded in with atomicMin / atomicMax (device-side
 // timing for launches inside a graph loop, where events cannot accumulate).
-template <int D, typename T, bool FINAL, bool GEN>
+template <int D, typename T, bool FINAL, bool GEN, typename S = T>
 __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 4 : 1)
-k_map(PView<T> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
+k_map(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
       double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
       double *__restrict__ psum, unsigned long long *__restrict__ tim) {
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
-  map_block<D, T, FINAL, GEN>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes, nodes_u, J, pg,
-                              kc, ms, cnt, psum + 2 * (size_t)blockIdx.x);
+  map_block<D, T, FINAL, GEN, S>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes, nodes_u, J,
+                                 pg, kc, ms, cnt, psum + 2 * (size_t)blockIdx.x);
   if (tim) {
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(tim + 1, global_ns());

@@ -512,7 +512,27 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
                          ctx->Jorb, pg, kconst<RT>(sc_in, pg), ctx->cnt_dev, ctx->psum, tim)))
     // the general kernels (degree-one shapes, refinement) only when needed
     const bool gen = sc_in.order != 2 || sc_in.refine_max > 0;
-    if (final_pass) {
+    if (ctx->eval_f32) {  // FP32 arithmetic on the FP64 particle storage
+#define PIC_MAP_F32(DD, FIN, GEN)                                                          \
+  k_map<DD, float, FIN, GEN, double><<<nb, kPT, 0, ctx->st>>>(                               \
+      pview<double>(ctx), ctx->nodes_f, ctx->nodes_u_f, ctx->Jorb, pg, kconst<float>(sc_in, pg), \
+      ctx->cnt_dev, ctx->psum, tim)
+#define PIC_MAP_F32_D(FIN, GEN)                                                            \
+  do {                                                                                     \
+    if (ctx->g.dim == 1) PIC_MAP_F32(1, FIN, GEN);                                         \
+    else if (ctx->g.dim == 2) PIC_MAP_F32(2, FIN, GEN);                                    \
+    else PIC_MAP_F32(3, FIN, GEN);                                                         \
+  } while (0)
+      // the FP32 stage runs plain evaluations of the common path only
+      // (pic_init admits fp32_first with quadratic shapes and no refinement)
+      if (final_pass || gen) {
+        ctx->err = "FP32 stage: final pass or general shapes requested";
+        return PIC_EARG;
+      }
+      PIC_MAP_F32_D(false, false);
+#undef PIC_MAP_F32_D
+#undef PIC_MAP_F32
+    } else if (final_pass) {
       if (gen) PIC_MAP_LAUNCH(true, true);
       else PIC_MAP_LAUNCH(true, false);
     } else {

@@ -65,7 +65,8 @@ void free_all(pic_ctx *ctx) {
                   ctx->work_h, ctx->A1_real, ctx->scr_r, ctx->nodes, ctx->nodes_u, ctx->Jorb,
                   ctx->Jorb_h, ctx->H, ctx->j, ctx->r, ctx->jt, ctx->Ht, ctx->rt, ctx->dir,
                   ctx->dJ, ctx->dR, ctx->tw[0], ctx->tw[1], ctx->tw[2], ctx->red, ctx->cnt_dev,
-                  ctx->A_real_f, ctx->cnt_sort, ctx->keys, ctx->tmp_l};
+                  ctx->A_real_f, ctx->cnt_sort, ctx->keys, ctx->tmp_l, ctx->nodes_f,
+                  ctx->nodes_u_f};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->red_host) cudaFreeHost(ctx->red_host);
@@ -95,6 +96,10 @@ int alloc_mesh(pic_ctx *ctx) {
   CK(cudaMalloc((void **)&ctx->dR, R * 3 * Ng * M));
   CK(cudaMalloc(&ctx->nodes, (size_t)ctx->rsize * node_record_len((int)d) * Ng));
   CK(cudaMalloc(&ctx->nodes_u, (size_t)ctx->rsize * 4 * Ng));
+  if (ctx->opt.fp32_first) {
+    CK(cudaMalloc((void **)&ctx->nodes_f, sizeof(float) * node_record_len((int)d) * Ng));
+    CK(cudaMalloc((void **)&ctx->nodes_u_f, sizeof(float) * 4 * Ng));
+  }
   // block partials of the reductions: compensated (sum, error) pairs of up
   // to 3 quantities per block (field.cu), 8 doubles per block (reduce.cu)
   size_t nred = 8 * (Ng / 256 + 2) + 1024 * 48 + 64;
@@ -519,7 +524,10 @@ int pic_init(pic_ctx **out, const pic_grid *grid, const pic_species *species, in
        o.nonlinear_solver != PIC_SOLVER_NEWTON_KRYLOV) ||
       (o.nonlinear_solver == PIC_SOLVER_NEWTON_KRYLOV &&
        (o.precision != PIC_FP64 || o.order != 2 || o.refine_max != 0 || o.inner_warm_start ||
-        o.deterministic_deposit)))
+        o.deterministic_deposit)) ||
+      (o.fp32_first && (o.precision != PIC_FP64 || o.order != 2 || o.refine_max != 0 ||
+                        o.nonlinear_solver != PIC_SOLVER_ANDERSON || o.host_control ||
+                        o.deterministic_deposit)))
     return PIC_EARG;
   // the deterministic deposit's node gather spans at least 5 nodes per dimension
   if (o.deterministic_deposit)
@@ -745,12 +753,33 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
   if (!ctx->opt.host_control && !newton) {
     // the whole outer iteration on the device (control.cu)
     StepOutcome so;
-    if ((e = step_control_device(ctx, sc, tr, ta, &so, &ran))) return e;
+    int from_j = 0, evals0 = 0, iters0 = 0;
+    if (ctx->opt.fp32_first) {
+      // FP32 stage: FP32 arithmetic on the FP64 particle state down to the
+      // FP32 floor of the tolerance, no verification; the FP64 iteration
+      // then continues from its last accepted current (fresh Anderson
+      // history: the map has changed)
+      const double t32 = std::max(tol, ctx->opt.mixed_tol_floor);
+      double tr32, ta32, itr32, ita32;
+      tolerances(ctx, t32, &tr32, &ta32, &itr32, &ita32);
+      ctx->eval_f32 = 1;
+      int ran32 = 0;
+      e = step_control_device(ctx, make_sc(ctx, itr32, ita32), tr32, ta32, &so, &ran32, 0, 0);
+      ctx->eval_f32 = 0;
+      if (e) return e;
+      if (ran32) {
+        from_j = 1;  // even a failed FP32 stage leaves an accepted iterate in j
+        evals0 = so.map_evals;
+        iters0 = so.outer_iters;
+        R.fp32_evals = so.map_evals;
+      }
+    }
+    if ((e = step_control_device(ctx, sc, tr, ta, &so, &ran, from_j, 1))) return e;
     if (ran) {
       status = so.status;
       done = status == PIC_OK;
-      R.outer_iters = so.outer_iters;
-      R.map_evals = so.map_evals;
+      R.outer_iters = iters0 + so.outer_iters;
+      R.map_evals = evals0 + so.map_evals;
       R.res_scaled_rms = so.res_srms;
       R.res_scaled_max = so.res_smax;
       ev.work_p = so.work_p;

@@ -131,6 +131,9 @@ struct pic_ctx {
   double *scr_r;      // 4Ng  real scratch (start, get/set)
   void *nodes;        // Ng * NV gather records in the particle real type
   void *nodes_u;      // Ng * 3 U^{n+1/2} records (final pass diagnostics)
+  float *nodes_f;     // Ng * NV FP32 gather records (option fp32_first), or null
+  float *nodes_u_f;   // Ng * 4 their U^{n+1/2} records
+  int eval_f32;       // the queued evaluations use FP32 arithmetic on FP64 storage
   double *Jorb;       // 3Ng deposited orbit current
   double2 *Jorb_h;    // 3Ng its projected transform
   double *H;          // 3Ng  H(j)
@@ -156,6 +159,7 @@ struct pic_ctx {
     const void *phi, *A;
     double tr, ta, itr, ita;
     int64_t np;
+    int f32;  // FP32-stage evaluations
     cudaGraphExec_t loop, verify;
     int nk_round, nk_verify;  // kernels per loop round, in the verification
   } sgraphs[4];
@@ -330,6 +334,7 @@ void nk_end(NkState *nk);
 // Algorithm 1's outer iteration decided on the device (one context)
 struct StepOutcome {
   int status, why, outer_iters, map_evals, inner_max;
+  int converged;  // the loop ended with the outer tests passed
   unsigned long long inner_sum, refined;  // of the final (verification) evaluation
   double res_srms, res_smax, work_p, chain;
 };
@@ -340,8 +345,11 @@ void control_graphs_clear(pic_ctx *ctx);
 // the graphs of control.cu; *ran = 0 when they cannot be used (the caller
 // then drives the step from the host).  On success of the step ctx->j holds
 // the accepted current, ctx->H its map value from the final evaluation.
+// from_j: start from the iterate already in ctx->j (a second stage) instead
+// of J_acc; verify: run the verifying evaluation after the loop (without
+// it the loop ends at the first iterate that passes the tests).
 int step_control_device(pic_ctx *ctx, const StepConst &sc, double tr, double ta, StepOutcome *out,
-                        int *ran);
+                        int *ran, int from_j, int verify);
 
 // ---------------------------------------------------------------- reduce.cu
 // queue r = H - j and its test sums (copied to pinned host memory);
