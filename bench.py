@@ -292,6 +292,54 @@ def run_two_stream_1d(args, barrier, flush, stream, peak64):
                            "bound": "launch/latency (32 CTAs of 128 threads)"}}
 
 
+# ---------------------------------------------------------------- differentiation workload
+DIFF = "two_stream_2d_256x256_100ppc"
+
+
+def run_differentiation(args, barrier, flush, stream):
+    """The differentiation workload (2D3V two-stream, 256^2 cells on a box of
+    side 4 pi, 100 particles/cell = 6,553,600, beams u_x = +-0.8, T = 1e-3,
+    dt = 0.05, tol 1e-10, FP64): one step's outer problem solved by
+    Algorithm 1's Anderson iteration and by the Newton-Krylov option
+    (GMRES(20) on Jacobian-vector products, dual-number map evaluations in
+    FP64), each timed over the same steps from the same state."""
+    import torch
+
+    import paper_2609_36383_b300 as P
+    import pic_inputs
+    cfg = pic_inputs.two_stream_2d()
+    npart = cfg["w"].shape[0]
+    out = {"workload": DIFF, "particles": npart, "tol": cfg["tol"],
+           "note": "Jacobian-vector products are FP64 dual-number map evaluations"}
+    for label, solver in (("anderson", P.PIC_SOLVER_ANDERSON),
+                          ("newton_krylov", P.PIC_SOLVER_NEWTON_KRYLOV)):
+        sim = P.from_config(cfg, precision=P.PIC_FP64, nonlinear_solver=solver)
+        sim.start()
+        sim.step(cfg["tol"], raise_on_fail=True)  # warm-up (graph capture, caches)
+        barrier()
+        ms, evals, jvps, outer = 0.0, [], [], []
+        for _ in range(3):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = sim.step(cfg["tol"], raise_on_fail=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            evals.append(r["map_evals"])
+            jvps.append(r["jvp_evals"])
+            outer.append(r["outer_iters"])
+        barrier()
+        sim.close()
+        out[label] = {"ms_per_step": ms / 3, "mean_map_evals_per_step": statistics.mean(evals),
+                      "mean_jvp_evals_per_step": statistics.mean(jvps),
+                      "mean_outer_iters": statistics.mean(outer)}
+    out["newton_krylov_time_vs_anderson"] = (out["newton_krylov"]["ms_per_step"]
+                                             / out["anderson"]["ms_per_step"])
+    return out
+
+
 # ---------------------------------------------------------------- large case
 LARGE = "weibel_2d_ions_512x512_256ppc"
 
@@ -410,7 +458,8 @@ def run_ours(args):
     # paper's cold-started inner iteration, and the FP64 path with the
     # optional warm start (inner tolerance 10x tighter)
     paths = (("fp64", P.PIC_FP64, {}), ("mixed", P.PIC_MIXED, {}),
-             ("fp64_warm", P.PIC_FP64, dict(inner_warm_start=1, inner_tol_scale=0.1)))
+             ("fp64_warm", P.PIC_FP64, dict(inner_warm_start=1, inner_tol_scale=0.1)),
+             ("fp32_first", P.PIC_FP64, dict(fp32_first=1)))
     if args.only:
         paths = tuple(p for p in paths if p[0] == args.only)
     # one clock sampler spans both timed regions (the mixed one alone is far
@@ -432,9 +481,10 @@ def run_ours(args):
             fp64_sim = sim
         else:
             sim.close()
-    ens = lg = ts1 = None
+    ens = lg = ts1 = dif = None
     if not (args.only or args.skip_e2e):
         ts1 = run_two_stream_1d(args, barrier, flush, stream, P.fma_throughput(P.PIC_FP64))
+        dif = run_differentiation(args, barrier, flush, stream)
         ens, ens_particles = run_ensemble(args, rank, barrier, flush, stream)
         if not args.no_large:
             lg = run_large(args, rank, barrier, flush, stream)
@@ -546,6 +596,7 @@ def run_ours(args):
                            "frac": achieved_m / peak32, "avg_ms": avg_ms_m,
                            "traffic": measured_traffic("mixed")},
         },
+        "fp32_first": fp32_first_summary(dist, results["fp32_first"], value, t_max, args.steps),
         "fp64_warm_start": {
             "value": warm_value, "ms_per_step": warm_ms / args.steps,
             "options": "inner_warm_start=1, inner_tol_scale=0.1",
@@ -565,6 +616,7 @@ def run_ours(args):
                     "frac": bytes_launch / (avg_ms * 1e-3) / 1e9 / hbm},
         },
         "two_stream_1d": ts1,
+        "differentiation": dif,
         "ensemble": ensemble_summary(dist, ens, ens_particles, args.steps),
         "large": large_summary(dist, lg, args.steps, peak32) if lg else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -578,6 +630,21 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def fp32_first_summary(dist, ff, fp64_value, fp64_ms, steps):
+    """FP64 steps whose outer iteration starts in FP32 arithmetic (option
+    fp32_first): FP64 results at the FP64 tolerance; the speedup is in step
+    time against the plain FP64 path at the same energy drift."""
+    v, t = aggregate(dist, ff["pushes"], ff["ms"], "cuda")
+    reps = ff["reports"]
+    return {"value": v, "unit": UNIT, "dtype": "f64 (FP32 stage, then FP64)",
+            "ms_per_step": t / steps, "max_abs_rel_dE": ff["rel_dE"],
+            "mean_fp32_evals_per_step": statistics.mean(r["fp32_evals"] for r in reps),
+            "mean_fp64_evals_per_step": statistics.mean(r["map_evals"] - r["fp32_evals"]
+                                                        for r in reps),
+            "step_speedup_vs_fp64": fp64_ms / t,
+            "note": "value counts FP32 and FP64 map evaluations alike"}
 
 
 def ensemble_summary(dist, ens, particles, steps):

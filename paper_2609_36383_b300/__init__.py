@@ -346,6 +346,84 @@ class Simulation:
         self._check(rc, allow=(PIC_EINNER,))
         return rc, H, jbar
 
+    # -- the same calls on device tensors (torch, float64, on this GPU) -------
+    @staticmethod
+    def _dev_in(t, n):
+        import torch
+        t = t.detach().to(torch.float64).contiguous().reshape(-1)
+        assert t.is_cuda and t.numel() == n
+        torch.cuda.current_stream().synchronize()  # torch's writes land before the library reads
+        return t
+
+    def eval_map_device(self, j, tol):
+        """H(j) for a device tensor j (3 Ng), as a device tensor."""
+        import torch
+        j = self._dev_in(j, 3 * self.Ng)
+        H = torch.empty_like(j)
+        rc = lib().pic_eval_map(self._h, _ptr(j, 1), float(tol), _ptr(H, 1), None, None, None, 1)
+        self._check(rc, allow=(PIC_EINNER,))
+        return rc, H
+
+    def eval_map_jvp_device(self, j, dj, tol):
+        """H(j) and H'(j) dj for device tensors, as device tensors."""
+        import torch
+        j, dj = self._dev_in(j, 3 * self.Ng), self._dev_in(dj, 3 * self.Ng)
+        H, dH = torch.empty_like(j), torch.empty_like(j)
+        rc = lib().pic_eval_map_jvp(self._h, _ptr(j, 1), _ptr(dj, 1), float(tol), _ptr(H, 1),
+                                    _ptr(dH, 1), 1)
+        self._check(rc, allow=(PIC_EINNER,))
+        return rc, H, dH
+
+    def eval_map_vjp_device(self, j, ybar, tol):
+        """H(j) and H'(j)^T ybar for device tensors, as device tensors."""
+        import torch
+        j, ybar = self._dev_in(j, 3 * self.Ng), self._dev_in(ybar, 3 * self.Ng)
+        H, jbar = torch.empty_like(j), torch.empty_like(j)
+        rc = lib().pic_eval_map_vjp(self._h, _ptr(j, 1), _ptr(ybar, 1), float(tol), _ptr(H, 1),
+                                    _ptr(jbar, 1), 1)
+        self._check(rc, allow=(PIC_EINNER,))
+        return rc, H, jbar
+
+    def particles_device(self):
+        """x (dim, N), P (3, N), w (N), species (N) as device tensors, load order."""
+        import torch
+        n = self.num_particles()
+        dev = dict(dtype=torch.float64, device="cuda")
+        x = torch.empty(self.dim * max(n, 1), **dev)
+        P = torch.empty(3 * max(n, 1), **dev)
+        w = torch.empty(max(n, 1), **dev)
+        sp = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        self._check(lib().pic_get_particles(self._h, _ptr(x, 1), _ptr(P, 1), _ptr(w, 1),
+                                            _ptr(sp, 1), 1))
+        return x[:self.dim * n].reshape(self.dim, n), P[:3 * n].reshape(3, n), w[:n], sp[:n]
+
+    def fields_device(self) -> dict:
+        """The potentials, rho and the accepted current as device tensors."""
+        import torch
+        N = self.Ng
+        dev = dict(dtype=torch.float64, device="cuda")
+        out = dict(phi=torch.empty(N, **dev), psi=torch.empty(N, **dev),
+                   A=torch.empty(3 * N, **dev), U=torch.empty(3 * N, **dev),
+                   rho=torch.empty(N, **dev), J=torch.empty(3 * N, **dev))
+        self._check(lib().pic_get_potentials(self._h, *[_ptr(out[k], 1) for k in
+                                                        ("phi", "psi", "A", "U", "rho", "J")], 1))
+        return out
+
+    def step_vjp_device(self, tol, xbar, Pbar, fbar):
+        """pic_step_vjp on device tensors: xbar (dim x N), Pbar (3 x N) in load
+        order and fbar (9 Ng, [phi, psi, A, U, rho]); returns the cotangents
+        before the step as device tensors of the same shapes."""
+        import torch
+        n = self.num_particles()
+        x1 = self._dev_in(xbar, self.dim * n)
+        P1 = self._dev_in(Pbar, 3 * n)
+        f1 = self._dev_in(fbar, 9 * self.Ng)
+        x0, P0, f0 = torch.empty_like(x1), torch.empty_like(P1), torch.empty_like(f1)
+        its = C.c_int(0)
+        self._check(lib().pic_step_vjp(self._h, float(tol), _ptr(x1, 1), _ptr(P1, 1), _ptr(f1, 1),
+                                       _ptr(x0, 1), _ptr(P0, 1), _ptr(f0, 1), C.byref(its), 1))
+        return x0.reshape(self.dim, n), P0.reshape(3, n), f0
+
     def tune_sort(self, tol, steps, candidates=(0, 1, 2, 5, 10, 20)):
         """Measure each candidate sort interval over `steps` steps from the
         current state, restore the state and keep the fastest; returns

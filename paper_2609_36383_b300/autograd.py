@@ -20,6 +20,9 @@
   particle and every mesh value.
 
 Argument marshalling only: every derivative is computed by the library.
+Tensors on the GPU go to the library as device pointers (no host copy);
+tensors on the host (and simulations without device calls) go through the
+host-array calls.
 """
 from __future__ import annotations
 
@@ -27,34 +30,55 @@ import numpy as np
 import torch
 
 
+def _on_device(sim, t: torch.Tensor) -> bool:
+    return t.is_cuda and hasattr(sim, "eval_map_device")
+
+
+def _host(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _check(rc):
+    if rc:
+        raise RuntimeError(f"map evaluation failed with status {rc}")
+
+
 class _MapEval(torch.autograd.Function):
     @staticmethod
     def forward(j, sim, tol):
-        rc, H, _, _, _ = sim.eval_map(j.detach().cpu().numpy().astype(np.float64), tol)
-        if rc:
-            raise RuntimeError(f"map evaluation failed with status {rc}")
+        if _on_device(sim, j):
+            rc, H = sim.eval_map_device(j, tol)
+            _check(rc)
+            return H
+        rc, H, _, _, _ = sim.eval_map(_host(j), tol)
+        _check(rc)
         return torch.from_numpy(H).to(j.device)
 
     @staticmethod
     def setup_context(ctx, inputs, output):
         j, sim, tol = inputs
         ctx.sim, ctx.tol = sim, tol
-        ctx.j = j.detach().cpu().numpy().astype(np.float64)
+        ctx.dev = _on_device(sim, j)
+        ctx.j = j.detach().clone() if ctx.dev else _host(j)
 
     @staticmethod
     def jvp(ctx, dj, _dsim, _dtol):
-        rc, _, dH = ctx.sim.eval_map_jvp(ctx.j, dj.detach().cpu().numpy().astype(np.float64),
-                                         ctx.tol)
-        if rc:
-            raise RuntimeError(f"map evaluation failed with status {rc}")
+        if ctx.dev:
+            rc, _, dH = ctx.sim.eval_map_jvp_device(ctx.j, dj, ctx.tol)
+            _check(rc)
+            return dH
+        rc, _, dH = ctx.sim.eval_map_jvp(ctx.j, _host(dj), ctx.tol)
+        _check(rc)
         return torch.from_numpy(dH).to(dj.device)
 
     @staticmethod
     def backward(ctx, gH):
-        rc, _, jbar = ctx.sim.eval_map_vjp(ctx.j, gH.detach().cpu().numpy().astype(np.float64),
-                                           ctx.tol)
-        if rc:
-            raise RuntimeError(f"map evaluation failed with status {rc}")
+        if ctx.dev:
+            rc, _, jbar = ctx.sim.eval_map_vjp_device(ctx.j, gH, ctx.tol)
+            _check(rc)
+            return jbar, None, None
+        rc, _, jbar = ctx.sim.eval_map_vjp(ctx.j, _host(gH), ctx.tol)
+        _check(rc)
         return torch.from_numpy(jbar).to(gH.device), None, None
 
 
@@ -125,6 +149,8 @@ class _StateAfter(torch.autograd.Function):
     def forward(x, P, f, sim, tol, steps):
         if steps < 1:
             raise ValueError("state_after needs at least one step")
+        if x.is_cuda and hasattr(sim, "particles_device"):
+            return _state_after_device(x, P, f, sim, tol, steps)
         _, _, w, sp = sim.particles()
         seed = sim.fields()["J"]
         E0 = sim.checkpoint_header()["E0"]
@@ -155,6 +181,12 @@ class _StateAfter(torch.autograd.Function):
     def backward(ctx, gx, gP, gf):
         sim = ctx.sim
         final = sim.checkpoint()
+        if gx.is_cuda and hasattr(sim, "step_vjp_device"):
+            for img in reversed(ctx.images):
+                sim.restore(img)
+                gx, gP, gf = sim.step_vjp_device(ctx.tol, gx, gP, gf)
+            sim.restore(final)
+            return gx, gP, gf, None, None, None
         g = {"x": gx.detach().cpu().numpy(), "P": gP.detach().cpu().numpy(),
              "fields": unpack_fields(gf.detach().cpu().numpy(), sim.Ng)}
         for img in reversed(ctx.images):
@@ -164,6 +196,34 @@ class _StateAfter(torch.autograd.Function):
         dev = gx.device
         return (torch.from_numpy(g["x"]).to(dev), torch.from_numpy(g["P"]).to(dev),
                 torch.from_numpy(pack_fields(g["fields"], sim.Ng)).to(dev), None, None, None)
+
+
+def _state_after_device(x, P, f, sim, tol, steps):
+    """The forward pass of state_after on device tensors: the state goes in
+    and comes out through the library's device-pointer calls."""
+    _, _, w, sp = sim.particles_device()
+    J = sim.fields_device()["J"]
+    E0 = sim.checkpoint_header()["E0"]
+    Ng = sim.Ng
+    fc = f.detach().to(torch.float64).contiguous()
+    fields, off = {}, 0
+    for k, nc in FIELD_PARTS:
+        fields[k] = fc[off:off + nc * Ng]
+        off += nc * Ng
+    fields["J"] = J
+    torch.cuda.current_stream().synchronize()
+    sim.set_state(x.detach().contiguous(), P.detach().contiguous(), w, sp, fields, E0,
+                  on_device=True)
+    images = []
+    for _ in range(steps):
+        images.append(sim.checkpoint())
+        r = sim.step(tol)
+        if r["status"]:
+            raise RuntimeError(f"step failed with status {r['status']}")
+    x1, P1, _, _ = sim.particles_device()
+    f1 = sim.fields_device()
+    sim._autograd_images = images  # kept for the backward sweep
+    return x1, P1, torch.cat([f1[k].reshape(-1) for k, _ in FIELD_PARTS])
 
 
 def state_after(sim, tol: float, steps: int, x: torch.Tensor, P: torch.Tensor, f: torch.Tensor):

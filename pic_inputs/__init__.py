@@ -26,6 +26,9 @@ workload sizes used here):
   100 at rest (same temperature in energy units) and no background.
 - ``two_stream_ensemble``: many independent ``two_stream_1d`` instances with
   drawn mesh sizes, particles per cell and beam velocities.
+- ``two_stream_2d``: 2D3V two-stream for the differentiation workload; box of
+  side 4 pi, 256^2 cells, beams u_x = +-0.8 with Maxwell-Juettner T = 1e-3,
+  100 particles/cell (6,553,600), density seed 1e-3 cos k x, dt = 0.05.
 """
 from __future__ import annotations
 
@@ -184,6 +187,40 @@ def weibel_2d_ions(n=512, ppc_beam=64, ppc_ion=128, u_drift=0.9, T=0.05, mass_ra
                 u=np.concatenate([e["u"], ui], axis=1), w=np.concatenate([we, wi]),
                 sp=np.concatenate([np.zeros(ne, np.int32), np.ones(ni, np.int32)]),
                 A=e["A"], U=None)
+
+
+def two_stream_2d(n=256, ppc_beam=50, u_drift=0.8, T=1e-3, k=0.5, pert=1e-3, dt=0.05,
+                  tol=1e-10, steps=50, seed=0):
+    """2D3V relativistic two-stream (the differentiation workload): a square
+    box of side 2 pi / k (k = 0.5: L = 4 pi), n^2 cells, counter-streaming
+    electron beams u_x = +-u_drift with a Maxwell-Juettner spread of
+    temperature T, ppc_beam particles per cell per beam at uniform random
+    positions, weights (rho0 L^2 / N)(1 + pert cos k x), a fixed
+    neutralising background.  Each particle's beam sign (+1 or -1) is
+    returned as `beam`, so that a drift derivative can be seeded."""
+    rng = np.random.default_rng(seed)
+    Lx = 2.0 * math.pi / k
+    L = [Lx, Lx]
+    x0 = [-0.5 * Lx, -0.5 * Lx]
+    ncell = n * n
+    nb = ncell * ppc_beam
+    dx = Lx / n
+    cells = np.repeat(np.arange(ncell), ppc_beam)
+    xs, us, beam = [], [], []
+    for sgn in (1.0, -1.0):
+        px = x0[0] + (cells % n + rng.random(nb)) * dx
+        py = x0[1] + (cells // n + rng.random(nb)) * dx
+        xs.append(np.stack([px, py]))
+        us.append(drifting_mj(rng, T, sgn * u_drift, 0, nb))
+        beam.append(np.full(nb, sgn))
+    x = np.concatenate(xs, axis=1)
+    u = np.concatenate(us, axis=1)
+    N = x.shape[1]
+    w = (Lx * Lx / N) * (1.0 + pert * np.cos(k * (x[0] - x0[0])))
+    return dict(name=f"two_stream_2d_{n}x{n}_{2 * ppc_beam}ppc", dim=2, n=[n, n], L=L, x0=x0,
+                species=[(-1.0, 1.0)], rho_bg=1.0, dt=dt, tol=tol, steps=steps,
+                x=x, u=u, w=w, sp=np.zeros(N, np.int32), A=None, U=None,
+                beam=np.concatenate(beam))
 
 
 def thermal_box(dim=3, n=8, ppc=2, T=0.05, u_drift=0.3, dt=0.1, tol=1e-12, seed=0,

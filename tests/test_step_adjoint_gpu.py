@@ -303,3 +303,49 @@ def test_vacuum_step_adjoint_is_the_transpose_of_the_field_step(project):
     gross = sum(np.sum(np.abs(yb[k] * (moved[k] - base[k]))) for k in yb)
     print(f"project {project}: <ybar, step dS> {lhs:.14e}, <step^T ybar, dS> {rhs:.14e}")
     assert abs(lhs - rhs) <= 1e-12 * gross
+
+
+def test_autograd_wrappers_on_device_tensors_match_host_tensors():
+    """The torch.autograd wrappers with CUDA tensors (device pointers into the
+    library, no host copy of the tensors) give what they give with host
+    tensors: state_after's gradient through two steps, and map_eval's value,
+    forward- and reverse-mode derivatives."""
+    import torch
+    import torch.autograd.forward_ad as fwAD
+    from paper_2609_36383_b300 import autograd as pa
+    cfg = small_2d()
+    s = make_gpu(cfg)
+    s.start()
+    assert s.step(TOL)["status"] == 0
+    x0, P0, _, _ = s.particles()
+    f0 = pa.pack_fields(s.fields(), s.Ng)
+    base = s.checkpoint()
+    rng = np.random.default_rng(5)
+    c = [rng.standard_normal(x0.shape), rng.standard_normal(P0.shape),
+         rng.standard_normal(f0.shape)]
+    grads = {}
+    for dev in ("cpu", "cuda"):
+        s.restore(base)
+        x, P, f = (torch.tensor(a, device=dev, requires_grad=True) for a in (x0, P0, f0))
+        out = pa.state_after(s, TOL, 2, x, P, f)
+        assert all(t.device.type == dev for t in out)
+        loss = sum((torch.tensor(ci, device=dev) * t).sum() for ci, t in zip(c, out))
+        loss.backward()
+        grads[dev] = [g.grad.detach().cpu().numpy() for g in (x, P, f)]
+    for a, b in zip(grads["cpu"], grads["cuda"]):
+        assert np.abs(a - b).max() <= 1e-9 * max(np.abs(a).max(), 1e-300)
+    s.restore(base)
+    j0 = s.fields()["J"]
+    dj = rng.standard_normal(j0.shape) * np.abs(j0).max()
+    ybar = rng.standard_normal(j0.shape)
+    res = {}
+    for dev in ("cpu", "cuda"):
+        j = torch.tensor(j0, device=dev, requires_grad=True)
+        with fwAD.dual_level():
+            jd = fwAD.make_dual(j.detach(), torch.tensor(dj, device=dev))
+            H, dH = fwAD.unpack_dual(pa.map_eval(s, jd, TOL))
+        Hr = pa.map_eval(s, j, TOL)
+        (Hr * torch.tensor(ybar, device=dev)).sum().backward()
+        res[dev] = [t.detach().cpu().numpy() for t in (H, dH, j.grad)]
+    for a, b in zip(res["cpu"], res["cuda"]):
+        assert np.abs(a - b).max() <= 1e-10 * max(np.abs(a).max(), 1e-300)
