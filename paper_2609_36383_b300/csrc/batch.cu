@@ -39,6 +39,7 @@
 // Per-instance initial states (pic_start) are prepared by a temporary
 // single-problem context per distinct grid and copied in.
 #include "map_device.cuh"
+#include "csum.cuh"
 #include "trace.cuh"
 
 #include <algorithm>
@@ -235,6 +236,17 @@ __device__ double block_sum(double v, double *sh) {
   __syncthreads();
   double s = 0.0;
   for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[w];
+  return s;
+}
+
+// compensated block sum (every addition a TwoSum; the total in every thread)
+__device__ CSum block_csum(CSum v, CSum *sh) {
+  v = csum_warp(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  CSum s = csum_zero();
+  for (int w = 0; w < (int)(blockDim.x >> 5); w++) s = csum_merge(s, sh[w]);
   return s;
 }
 
@@ -750,6 +762,7 @@ k_bmap(PView<T> pv, const int32_t *__restrict__ blk2inst, const BInst *__restric
 // the particle and mesh work sums (Eq. work-diagnostic) and the chain sum.
 __global__ void __launch_bounds__(kBT) k_bresid(BMesh p, double tau_r, double tau_a, int project) {
   __shared__ double sh[kBT / 32];
+  __shared__ CSum shc[kBT / 32];
   __shared__ double s_nyq[3];
   __shared__ double s_dots[kNDots];
   const int b = blockIdx.x;
@@ -769,7 +782,9 @@ __global__ void __launch_bounds__(kBT) k_bresid(BMesh p, double tau_r, double ta
     if (threadIdx.x == 0) s_nyq[c] = project ? v / N : 0.0;
   }
   __syncthreads();
-  double r2 = 0.0, h2 = 0.0, j2 = 0.0, mx = 0.0, work = 0.0;
+  // the outer tests' norms and the mesh work sum: compensated
+  CSum r2 = csum_zero(), h2 = csum_zero(), j2 = csum_zero(), work = csum_zero();
+  double mx = 0.0;
   for (int g = threadIdx.x; g < N; g += blockDim.x) {
     double rr = 0.0, hh = 0.0, jj = 0.0;
     for (int c = 0; c < 3; c++) {
@@ -781,25 +796,25 @@ __global__ void __launch_bounds__(kBT) k_bresid(BMesh p, double tau_r, double ta
       rr += rv * rv;
       hh += hv * hv;
       jj += jv * jv;
-      if (mode == B_FINAL) work += hv * p.Eh[q];
+      if (mode == B_FINAL) csum_add(work, hv * p.Eh[q]);
     }
-    r2 += rr;
-    h2 += hh;
-    j2 += jj;
+    csum_add(r2, rr);
+    csum_add(h2, hh);
+    csum_add(j2, jj);
     mx = fmax(mx, sqrt(rr) / (tau_a + 0.5 * tau_r * (sqrt(hh) + sqrt(jj))));
   }
-  r2 = block_sum(r2, sh);
-  h2 = block_sum(h2, sh);
-  j2 = block_sum(j2, sh);
+  r2 = block_csum(r2, shc);
+  h2 = block_csum(h2, shc);
+  j2 = block_csum(j2, shc);
   mx = block_max(mx, sh);
-  work = block_sum(work, sh);
+  work = block_csum(work, shc);
   BRes *R = p.res + b;
   if (threadIdx.x == 0) {
-    R->r2 = r2;
-    R->h2 = h2;
-    R->j2 = j2;
+    R->r2 = csum_value(r2);
+    R->h2 = csum_value(h2);
+    R->j2 = csum_value(j2);
     R->smax = mx;
-    R->work_mesh = work * in.dx;
+    R->work_mesh = csum_value(work) * in.dx;
   }
   __syncthreads();  // every r_t written
   // Gram products: the warps take the pairs in turn
@@ -826,17 +841,17 @@ __global__ void __launch_bounds__(kBT) k_bresid(BMesh p, double tau_r, double ta
     if (lane == 0) s_dots[d] = v;
   }
   // final pass: particle work and chain sums of the instance's blocks
-  double wp = 0.0, ch = 0.0;
+  CSum wp = csum_zero(), ch = csum_zero();
   if (mode == B_FINAL)
     for (int k = threadIdx.x; k < in.nblk; k += blockDim.x) {
-      wp += p.psum[2 * (int64_t)(in.blk0 + k)];
-      ch += p.psum[2 * (int64_t)(in.blk0 + k) + 1];
+      csum_add(wp, p.psum[2 * (int64_t)(in.blk0 + k)]);
+      csum_add(ch, p.psum[2 * (int64_t)(in.blk0 + k) + 1]);
     }
-  wp = block_sum(wp, sh);  // its barriers also publish s_dots
-  ch = block_sum(ch, sh);
+  wp = block_csum(wp, shc);  // its barriers also publish s_dots
+  ch = block_csum(ch, shc);
   if (threadIdx.x == 0) {
-    R->work_p = wp;
-    R->chain = ch;
+    R->work_p = csum_value(wp);
+    R->chain = csum_value(ch);
   }
   for (int d = threadIdx.x; d < npairs; d += blockDim.x) R->dots[d] = s_dots[d];
 }
@@ -945,14 +960,17 @@ k_bkinetic(PView<T> pv, const int32_t *__restrict__ blk2inst, const BInst *__res
     const T gam = sqrt(T(1) + p2 * im * im / (kc.kappa * kc.kappa));
     k = p2 * im / (gam + T(1));
   }
+  // a warp sums its 32 positive terms plainly; the warps merge with TwoSum
+  // into the block's (sum, error) pair
   for (int o = 16; o > 0; o >>= 1) k += __shfl_down_sync(0xffffffffu, k, o);
   __shared__ double sh[kPT / 32];
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = widen(k);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kPT / 32; w++) t += sh[w];
-    psum[blockIdx.x] = t;
+    CSum t = csum_zero();
+    for (int w = 0; w < kPT / 32; w++) csum_add(t, sh[w]);
+    psum[2 * (int64_t)blockIdx.x] = t.s;
+    psum[2 * (int64_t)blockIdx.x + 1] = t.c;
   }
 }
 
@@ -963,14 +981,17 @@ __global__ void __launch_bounds__(kBT)
 k_bdiag(const BInst *__restrict__ inst, const double *__restrict__ psum, const double2 *phi,
         const double2 *psi, const double2 *rho, const double2 *A, const double2 *U,
         double sigma1, double sigma2, double kap2, double *out) {
-  __shared__ double sh[kBT / 32];
+  __shared__ CSum shc[kBT / 32];
   const int b = blockIdx.x;
   const BInst in = inst[b];
   const int N = in.nx;
   const double twopiL = 2.0 * M_PI / in.L;
-  double K = 0.0;
-  for (int k = threadIdx.x; k < in.nblk; k += blockDim.x) K += psum[in.blk0 + k];
-  double w = 0.0, gs = 0.0, ls = 0.0;
+  // every sum compensated, as in the single-problem context
+  CSum K = csum_zero();
+  for (int k = threadIdx.x; k < in.nblk; k += blockDim.x)
+    K = csum_merge(K, CSum{psum[2 * (int64_t)(in.blk0 + k)],
+                           psum[2 * (int64_t)(in.blk0 + k) + 1]});
+  CSum w = csum_zero(), gs = csum_zero(), ls = csum_zero();
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const bool nyq = k == N / 2;
     const int kk = k < N / 2 ? k : k - N;
@@ -993,24 +1014,24 @@ k_bdiag(const BInst *__restrict__ inst, const double *__restrict__ psum, const d
     // B = curl A with d/dy = d/dz = 0: (0, -i k A_z, i k A_y)
     const double b2 = kx * kx * (Ah[1].x * Ah[1].x + Ah[1].y * Ah[1].y +
                                  Ah[2].x * Ah[2].x + Ah[2].y * Ah[2].y);
-    w += e2 / (2.0 * sigma1) + b2 / (2.0 * sigma2);
+    csum_add(w, e2 / (2.0 * sigma1) + b2 / (2.0 * sigma2));
     const double2 rr = rho[in.moff + k], ps = psi[in.moff + k];
     const double2 divU = cmi(kx, Uh[0]), divA = cmi(kx, Ah[0]);
     const double RGx = kx * kx * ph.x - divU.x - sigma1 * rr.x;
     const double RGy = kx * kx * ph.y - divU.y - sigma1 * rr.y;
     const double RLx = ps.x / kap2 + divA.x, RLy = ps.y / kap2 + divA.y;
-    gs += RGx * RGx + RGy * RGy;
-    ls += RLx * RLx + RLy * RLy;
+    csum_add(gs, RGx * RGx + RGy * RGy);
+    csum_add(ls, RLx * RLx + RLy * RLy);
   }
-  K = block_sum(K, sh);
-  w = block_sum(w, sh);
-  gs = block_sum(gs, sh);
-  ls = block_sum(ls, sh);
+  K = block_csum(K, shc);
+  w = block_csum(w, shc);
+  gs = block_csum(gs, shc);
+  ls = block_csum(ls, shc);
   if (threadIdx.x == 0) {
-    out[4 * b] = K;
-    out[4 * b + 1] = w * in.dx / N;
-    out[4 * b + 2] = sqrt(gs) / N;
-    out[4 * b + 3] = sqrt(ls) / N;
+    out[4 * b] = csum_value(K);
+    out[4 * b + 1] = csum_value(w) * in.dx / N;
+    out[4 * b + 2] = sqrt(csum_value(gs)) / N;
+    out[4 * b + 3] = sqrt(csum_value(ls)) / N;
   }
 }
 

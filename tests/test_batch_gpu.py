@@ -214,3 +214,37 @@ def test_batch_rejects_bad_arguments():
     bt = P.Batch([16, 16], [1.0, 1.0], [0.0, 0.0], [0, 0], [(-1.0, 1.0)], 0.1)
     with pytest.raises(P.PicError):
         bt.start()  # instances not staged
+
+
+@pytest.mark.parametrize("precision,tol,bound", [(0, 1e-12, 1e-9), (1, 1e-10, 2e-5)],
+                         ids=["fp64", "mixed"])
+def test_batch_production_sizes_match_single_contexts(precision, tol, bound):
+    """Instances at the ensemble workload's extremes: 512 cells with 256
+    particles per cell at u = 0.95 (131,072 particles, the largest mesh and
+    per-instance particle count the workload draws, the fastest beams), 256
+    cells with 128 per cell, and 32 cells with 16 per cell at u = 0.2, through
+    the shared-memory spectral solve and the persistent batch map, against
+    single-problem contexts with the same data, FP64 and FP32-mixed."""
+    cfgs = [pic_inputs.two_stream_1d(nx=512, ppc_beam=128, u0=0.95, tol=tol, seed=7),
+            pic_inputs.two_stream_1d(nx=256, ppc_beam=64, u0=0.6, tol=tol, seed=8),
+            pic_inputs.two_stream_1d(nx=32, ppc_beam=8, u0=0.2, tol=tol, seed=9)]
+    bt = _make_batch(cfgs, precision=precision)
+    bt.start()
+    singles = [make_gpu(c, precision=precision) for c in cfgs]
+    for s in singles:
+        s.start()
+    for st in range(3):
+        rb = bt.step(tol)
+        rs = [s.step(tol) for s in singles]
+        for b in range(len(cfgs)):
+            assert rb[b]["status"] == 0 and rs[b]["status"] == 0, (b, rb[b], rs[b])
+            assert rb[b]["E_tot"] == pytest.approx(rs[b]["E_tot"], rel=bound), b
+            if precision == 0:
+                assert abs(rb[b]["rel_dE"]) < 1e-11, (b, rb[b])
+                assert abs(rb[b]["map_evals"] - rs[b]["map_evals"]) <= 2
+    for b, c in enumerate(cfgs):
+        xb, Pb, _, _ = bt.particles(b)
+        xs, Ps, _, _ = singles[b].particles()
+        _assert_state_close(xb, Pb, bt.fields(b), xs, Ps, singles[b].fields(), c, bound)
+    for s in singles:
+        s.close()
