@@ -539,6 +539,14 @@ bool build_step_graphs(pic_ctx *ctx, const StepConst &sc, double tr, double ta,
   }
   if (ok) ok = cudaGraphInstantiate(&out.loop, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
+  if (ctx->eval_f32) {  // the FP32 stage never verifies: no verification graph
+    out.nk_verify = 0;
+    ctx->launches = before;
+    ctx->loop_capture = 0;
+    cudaGetLastError();
+    if (!ok) destroy_entry(out);
+    return ok;
+  }
   // verification graph: the condition kernel, then a conditional if node
   cudaGraph_t g2 = nullptr;
   cudaGraphConditionalHandle cv = 0;
@@ -620,7 +628,9 @@ void control_free(pic_ctx *ctx) {
 int step_control_device(pic_ctx *ctx, const StepConst &sc, double tr, double ta, StepOutcome *out,
                         int *ran, int from_j, int verify) {
   *ran = 0;
-  if (ctx->sgraphs_off || ctx->graphs_off || ctx->np == 0 || !ctx->sctl) return PIC_OK;
+  if (ctx->sgraphs_off || ctx->graphs_off || ctx->np == 0 || !ctx->sctl ||
+      (ctx->eval_f32 && ctx->f32_stage_off) || (verify && ctx->eval_f32))
+    return PIC_OK;
   pic_ctx::StepGraphs *ent = nullptr;
   for (int k = 0; k < ctx->nsgraphs; k++) {
     pic_ctx::StepGraphs &g = ctx->sgraphs[k];
@@ -634,8 +644,11 @@ int step_control_device(pic_ctx *ctx, const StepConst &sc, double tr, double ta,
     if (ctx->nsgraphs == 4) control_graphs_clear(ctx);
     pic_ctx::StepGraphs &g = ctx->sgraphs[ctx->nsgraphs];
     if (!build_step_graphs(ctx, sc, tr, ta, g)) {
-      ctx->sgraphs_off = 1;
-      return PIC_OK;  // the host drives the step
+      // the host drives the step; a refused FP32-stage graph only drops
+      // the FP32 stage
+      if (ctx->eval_f32) ctx->f32_stage_off = 1;
+      else ctx->sgraphs_off = 1;
+      return PIC_OK;
     }
     g.phi = ctx->phi_h;
     g.A = ctx->A_real;

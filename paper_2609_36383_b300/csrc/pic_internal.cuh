@@ -165,6 +165,7 @@ struct pic_ctx {
   } sgraphs[4];
   int nsgraphs;
   int sgraphs_off;               // the graphs could not be built: the host drives the step
+  int f32_stage_off;             // the FP32 stage's graph could not be built: no FP32 stage
   // ---- statistics (pic_stats) ------------------------------------------
   long long launches;          // kernels launched by this context
   long long map_launches;      // particle-map kernel launches
