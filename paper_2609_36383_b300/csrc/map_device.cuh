@@ -29,6 +29,7 @@
 #include "pic_internal.cuh"
 
 #include <cmath>
+#include <type_traits>
 
 namespace {
 
@@ -1349,6 +1350,271 @@ __device__ __forceinline__ void map_block(const PView<S> &pv, const int64_t i_sl
   }
 }
 
+// ---- the particle map with lane refill -----------------------------------
+//
+// A warp executes each inner sweep for as long as its slowest lane still
+// iterates, so in map_block the lanes whose particles converged early idle
+// until the warp's last particle converges.  map_chunk removes that wait: a
+// CTA owns a chunk of kRefill * kPT particles, and a lane whose particle has
+// converged (or failed) stores it and takes the next particle of the chunk
+// from a shared counter, so the sweeps run with full warps until the chunk
+// runs dry.  The chunk is ordered by the predicted number of knot planes
+// crossed (as in map_block) so that the particles a warp holds at one time
+// walk similar numbers of orbit pieces.  The deposits follow in a second
+// phase, over the chunk in that order, from the stored orbit velocities.
+// Every particle's arithmetic is that of map_block: only which lane
+// computes it, and when, changes.
+constexpr int kRefill = 4;
+constexpr int kChunk = kRefill * kPT;
+
+// one particle's inner solve between sweeps
+template <int D, typename T>
+struct LaneSolve {
+  PushConst<T> pc;
+  int cell[3];
+  T off[3], dtdx[3], vb[3], Pn1[3];
+  int it;
+};
+
+template <int D, typename T, typename S>
+__device__ __forceinline__ void lane_init(LaneSolve<D, T> &ls, const PView<S> &pv, int64_t i,
+                                          const KConst<T> &kc, const MapScale<T> &ms) {
+  const int64_t cap = pv.cap;
+  const int s_id = pv.sp[i];
+  PushConst<T> &pc = ls.pc;
+  pc.q = (T)(pv.w[i] * kc.qs[s_id]);
+  pc.m = (T)(pv.w[i] * kc.ms[s_id]);
+  const T kap = kc.kappa, dt = kc.dt;
+  pc.inv_m = T(1) / pc.m;
+  pc.mk = pc.m * kap;
+  pc.inv_mk = pc.inv_m / kap;
+  pc.hq = T(0.5) * pc.q * dt;
+  pc.a_hc = pc.hq * pc.inv_m;
+#pragma unroll
+  for (int l = 0; l < 3; l++) {
+    ls.cell[l] = l < D ? pv.cell[l * cap + i] : 0;
+    ls.off[l] = l < D ? (T)pv.off[l * cap + i] : T(0);
+    ls.dtdx[l] = l < D ? dt * ms.inv_dx[l] : T(0);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    pc.Pn[c] = (T)pv.P[c * cap + i];
+    pc.Am[c] = (T)pv.Am[c * cap + i];
+    pc.pn[c] = pc.Pn[c] - pc.q * pc.Am[c];
+    ls.vb[c] = (T)(kc.warm ? pv.vbar[c * cap + i] : pv.v0[c * cap + i]);
+    ls.Pn1[c] = pc.Pn[c];
+  }
+  pc.gamma_n = sqrt(T(1) + (pc.pn[0] * pc.pn[0] + pc.pn[1] * pc.pn[1] + pc.pn[2] * pc.pn[2]) *
+                               pc.inv_mk * pc.inv_mk);
+  ls.it = 0;
+}
+
+// One inner sweep of the particle a lane holds (the body of picard's loop):
+// 0 = not converged yet, 1 = converged, 2 = failed (status bits in sl).
+template <int D, typename T>
+__device__ __forceinline__ int lane_sweep(LaneSolve<D, T> &ls, const T *__restrict__ nodes,
+                                          const PGeom &pg, const KConst<T> &kc,
+                                          const MapScale<T> &ms, int &npieces,
+                                          unsigned int &sl) {
+  ls.it++;
+  T gphi[3], Dm[3][3], Ap[3];
+  if (!orbit_gather<D, T, false>(ls.cell, ls.off, ls.dtdx, T(0), T(1), nodes, pg, kc, ms, ls.vb,
+                                 gphi, Dm, Ap, npieces, 2)) {
+    sl |= PIC_ST_PIECES;
+    return 2;
+  }
+  T vn[3], Pc[3];
+  gmhc_push<D, T>(ls.pc, Ap, gphi, Dm, ls.vb, vn, Pc);
+  T diff = T(0), nrm = T(0), v2 = T(0);
+  bool fin = true;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    fin = fin && isfinite(vn[c]);
+    diff = fmax(diff, fabs(vn[c] - ls.vb[c]));
+    nrm = fmax(nrm, fabs(vn[c]));
+    v2 += vn[c] * vn[c];
+  }
+  if (!fin) {
+    sl |= PIC_ST_NONFINITE;
+    return 2;
+  }
+  if (v2 >= kc.kappa * kc.kappa) {
+    sl |= PIC_ST_SUPERLUM;
+    return 2;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    ls.vb[c] = vn[c];
+    ls.Pn1[c] = Pc[c];
+  }
+  if (diff <= kc.tau_a + kc.tau_r * nrm) return 1;
+  if (ls.it >= kc.inner_max) {
+    sl |= PIC_ST_NOCONV;
+    return 2;
+  }
+  return 0;
+}
+
+// The particle map over one chunk of kChunk particle slots starting at c0
+// (the common path: quadratic shapes, no refinement).  psum[0..2) receives
+// the CTA's final-pass partial sums.
+template <int D, typename T, bool FINAL, typename S>
+__device__ __forceinline__ void map_chunk(const PView<S> &pv, const int64_t c0,
+                                          const T *__restrict__ nodes,
+                                          const T *__restrict__ nodes_u, double *__restrict__ J,
+                                          const PGeom &pg, const KConst<T> &kc,
+                                          const MapScale<T> &ms, EvalCounters *__restrict__ cnt,
+                                          double *__restrict__ psum) {
+  __shared__ int s_order[kChunk];
+  __shared__ int s_wcnt[kRefill][kPT / 32][4];
+  __shared__ int s_next;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nvalid64 = pv.np - c0;
+  const int nvalid = nvalid64 < kChunk ? (int)nvalid64 : kChunk;
+  // 1. order the chunk by predicted crossing class (stable, deterministic)
+  int cls_of[kRefill];
+  unsigned mine[kRefill];
+#pragma unroll
+  for (int q = 0; q < kRefill; q++) {
+    const int k = q * kPT + threadIdx.x;
+    int cls = 3;
+    if (k < nvalid) {
+      const int64_t i = c0 + k;
+      cls = 0;
+#pragma unroll
+      for (int l = 0; l < D; l++) {
+        const T u = (T)pv.off[l * pv.cap + i] +
+                    (T)(kc.warm ? pv.vbar[l * pv.cap + i] : pv.v0[l * pv.cap + i]) * kc.dt *
+                        ms.inv_dx[l];
+        cls += (u >= T(0.5) || u < T(-0.5)) ? 1 : 0;
+      }
+      cls = cls < 2 ? cls : 2;
+    }
+    cls_of[q] = cls;
+    mine[q] = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      const unsigned b = __ballot_sync(0xffffffffu, cls == c);
+      if (lane == 0) s_wcnt[q][wid][c] = __popc(b);
+      if (cls == c) mine[q] = b;
+    }
+  }
+  if (threadIdx.x == 0) s_next = 0;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kRefill; q++) {
+    const int cls = cls_of[q];
+    int pos = __popc(mine[q] & ((1u << lane) - 1u));
+    for (int c = 0; c < cls; c++)
+      for (int qq = 0; qq < kRefill; qq++)
+        for (int w = 0; w < kPT / 32; w++) pos += s_wcnt[qq][w][c];
+    for (int qq = 0; qq < q; qq++)
+      for (int w = 0; w < kPT / 32; w++) pos += s_wcnt[qq][w][cls];
+    for (int w = 0; w < wid; w++) pos += s_wcnt[q][w][cls];
+    s_order[pos] = q * kPT + threadIdx.x;
+  }
+  __syncthreads();
+  // 2. the inner solves, lanes refilled from the chunk
+  int npieces = 0, mx_it = 0;
+  unsigned it_sum = 0;
+  unsigned int st = 0;
+  LaneSolve<D, T> ls;
+  int k = atomicAdd(&s_next, 1);
+  bool have = k < nvalid;
+  int64_t i = have ? c0 + s_order[k] : 0;
+  if (have) lane_init<D, T, S>(ls, pv, i, kc, ms);
+  while (__any_sync(0xffffffffu, have)) {
+    if (have) {
+      unsigned int sl = 0;
+      const int r = lane_sweep<D, T>(ls, nodes, pg, kc, ms, npieces, sl);
+      if (r != 0) {
+        const int64_t cap = pv.cap;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          pv.vbar[c * cap + i] = (S)ls.vb[c];
+          pv.Pnew[c * cap + i] = (S)ls.Pn1[c];
+        }
+        pv.iters[i] = r == 1 ? ls.it : -1;
+        if (r == 1) {
+          it_sum += (unsigned)ls.it;
+          mx_it = ls.it > mx_it ? ls.it : mx_it;
+        } else {
+          st |= sl;
+        }
+        k = atomicAdd(&s_next, 1);
+        have = k < nvalid;
+        if (have) {
+          i = c0 + s_order[k];
+          lane_init<D, T, S>(ls, pv, i, kc, ms);
+        }
+      }
+    }
+  }
+  __syncthreads();  // every orbit velocity of the chunk stored
+  // 3. the deposits, in class order, kPT particles at a time
+  double work = 0.0, chain = 0.0;
+  constexpr bool kWin = WarpWin<D>::kOn && sizeof(T) == 4;
+  __shared__ T s_win[kWin ? (kPT / 32) * WarpWin<D>::NE * 32 : 1];
+  T *win_warp = s_win + (size_t)wid * WarpWin<D>::NE * 32;
+  T *win_col = kWin ? win_warp + lane : nullptr;
+#pragma unroll 1
+  for (int q = 0; q < kRefill; q++) {
+    const int kk = q * kPT + threadIdx.x;
+    const int64_t ip = kk < nvalid ? c0 + s_order[kk] : -1;
+    const bool act = ip >= 0 && pv.iters[ip] > 0;
+    int ref[3] = {0, 0, 0};
+    if constexpr (kWin) {
+      const int64_t i0 = __shfl_sync(0xffffffffu, ip, 0);
+      if (i0 >= 0) {
+#pragma unroll
+        for (int l = 0; l < D; l++) ref[l] = pv.cell[l * pv.cap + i0];
+      }
+      for (int e = 0; e < WarpWin<D>::NE; e++) win_col[e * 32] = T(0);
+    }
+    if (act) {
+      LaneSolve<D, T> d;
+      lane_init<D, T, S>(d, pv, ip, kc, ms);
+#pragma unroll
+      for (int c = 0; c < 3; c++) d.vb[c] = (T)pv.vbar[c * pv.cap + ip];
+      deposit_orbit<D, T, FINAL, false>(d.pc, d.cell, d.off, d.dtdx, T(0), T(1), kc.dt, T(1),
+                                        d.vb, nodes, nodes_u, J, pg, kc, ms, win_col, ref,
+                                        npieces, st, work, chain, 2);
+    }
+    if constexpr (kWin) {
+      __syncwarp();
+      for (int e = lane; e < WarpWin<D>::NE; e += 32) {
+        const T *rowp = win_warp + (size_t)e * 32;
+        T sum = T(0);
+#pragma unroll 8
+        for (int l = 0; l < 32; l++) sum += rowp[(l + lane) & 31];
+        if (sum != T(0)) {
+          const int node = e / 3, c = e - 3 * node;
+          const int rx = node % WarpWin<D>::N0 + WarpWin<D>::LO0;
+          const int ry = node / WarpWin<D>::N0 + WarpWin<D>::LO1;
+          int g = (ref[0] + rx) & pg.mask[0];
+          if (D > 1) g += pg.n0 * ((ref[1] + ry) & pg.mask[1]);
+          atomicAdd(J + (size_t)c * pg.Ng + g, widen(sum));
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // counters: integer warp reductions, one atomic per warp
+  if (st) atomicOr(&cnt->status, st);
+  const unsigned it_w = __reduce_add_sync(0xffffffffu, it_sum);
+  const unsigned pc_w = __reduce_add_sync(0xffffffffu, (unsigned)npieces);
+  const int mx = __reduce_max_sync(0xffffffffu, mx_it);
+  if (lane == 0) {
+    atomicAdd(&cnt->inner_sum, (unsigned long long)it_w);
+    atomicAdd(&cnt->pieces, (unsigned long long)pc_w);
+    if (mx > 0) atomicMax(&cnt->inner_max, mx);
+  }
+  if (FINAL) {
+    double v[2] = {work, chain};
+    block_sums<2>(v, psum);
+  }
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1369,8 +1635,12 @@ k_map(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
       double *__restrict__ psum, unsigned long long *__restrict__ tim) {
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
-  map_block<D, T, FINAL, GEN, S>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes, nodes_u, J,
-                                 pg, kc, ms, cnt, psum + 2 * (size_t)blockIdx.x);
+  if constexpr (!GEN && (std::is_same<T, double>::value || std::is_same<T, float>::value))
+    map_chunk<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, nodes_u, J, pg, kc, ms, cnt,
+                              psum + 2 * (size_t)blockIdx.x);
+  else
+    map_block<D, T, FINAL, GEN, S>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes, nodes_u,
+                                   J, pg, kc, ms, cnt, psum + 2 * (size_t)blockIdx.x);
   if (tim) {
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(tim + 1, global_ns());

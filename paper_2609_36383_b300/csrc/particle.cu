@@ -506,6 +506,9 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
     const unsigned evf = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (!loop) CK(cudaEventRecordWithFlags(ctx->ev0, ctx->st, evf));
     unsigned long long *tim = loop ? ctx->map_timer : nullptr;
+    // the common path runs the lane-refill map over chunks of kChunk
+    // particles; the general path one particle per thread
+    if (!(sc_in.order != 2 || sc_in.refine_max > 0)) nb = (int)((ctx->np + kChunk - 1) / kChunk);
 #define PIC_MAP_LAUNCH(FIN, GEN)                                                          \
   PIC_DISPATCH(ctx, (k_map<DD, RT, FIN, GEN><<<nb, kPT, 0, ctx->st>>>(                      \
                          pview<RT>(ctx), (const RT *)ctx->nodes, (const RT *)ctx->nodes_u, \
