@@ -225,7 +225,7 @@ def run_ensemble(args, rank, barrier, flush, stream):
                 # step again in the next call (its evaluations still count)
                 if r["status"] not in (0, -4, -5):
                     raise RuntimeError(f"ensemble step failed: {r}")
-                failed["n"] += r["status"] != 0
+                failed["n"] += int(r["status"] != 0)
                 pushes += n * int(r["map_evals"])
                 drift = max(drift, abs(float(r["rel_dE"])))
                 evals.append(int(r["map_evals"]))
@@ -390,30 +390,41 @@ def run_large(args, rank, barrier, flush, stream):
     import pic_inputs
     cfg = pic_inputs.weibel_2d_ions(seed=rank)
     npart = cfg["w"].shape[0]
-    sim = P.from_config(cfg, precision=P.PIC_MIXED, sort_every=10)
-    del cfg["x"], cfg["u"], cfg["w"], cfg["sp"]
-    sim.start()
-    for _ in range(args.warmup):
-        step_retrying(sim, cfg["tol"], npart)
-    sim.reset_stats()
-    barrier()
-    ms, pushes, drift, evals = 0.0, 0, 0.0, []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r, extra = step_retrying(sim, cfg["tol"], npart)
-        e1.record(stream)
-        e1.synchronize()
-        ms += e0.elapsed_time(e1)
-        pushes += npart * r["map_evals"] + extra
-        drift = max(drift, abs(r["rel_dE"]))
-        evals.append(r["map_evals"])
-    barrier()
-    st = sim.stats()
-    sim.close()
-    return dict(ms=ms, pushes=pushes, drift=drift, evals=evals, stats=st, particles=npart)
+
+    def run(precision, warmup, steps, **opts):
+        sim = P.from_config(cfg, precision=precision, sort_every=10, **opts)
+        sim.start()
+        for _ in range(warmup):
+            step_retrying(sim, cfg["tol"], npart)
+        sim.reset_stats()
+        barrier()
+        ms, pushes, drift, evals, f32 = 0.0, 0, 0.0, [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r, extra = step_retrying(sim, cfg["tol"], npart)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            pushes += npart * r["map_evals"] + extra
+            drift = max(drift, abs(r["rel_dE"]))
+            evals.append(r["map_evals"])
+            f32.append(r["fp32_evals"])
+        barrier()
+        st = sim.stats()
+        sim.close()
+        return dict(ms=ms, pushes=pushes, drift=drift, evals=evals, fp32_evals=f32, stats=st,
+                    particles=npart, steps=steps)
+
+    out = run(P.PIC_MIXED, args.warmup, args.steps)
+    if not args.no_large_fp64:
+        # FP64 steps of the same case (about 11 GB of FP64 particle state), plain
+        # and begun in FP32: the mixed path's speed at the FP64 energy drift
+        out["fp64"] = run(P.PIC_FP64, 1, 2)
+        out["fp32_first"] = run(P.PIC_FP64, 1, 2, fp32_first=1)
+    return out
 
 
 def large_summary(dist, lg, steps, peak32):
@@ -428,7 +439,24 @@ def large_summary(dist, lg, steps, peak32):
             "sort_every": 10, "l2": "inputs (about 7 GB of particle state) exceed L2",
             "map_kernel": {"share_of_step": st["map_ms"] / max(lg["ms"], 1e-9),
                            "achieved_tflops": ach / 1e12, "peak_tflops": peak32 / 1e12,
-                           "frac": ach / peak32, "avg_ms": avg}}
+                           "frac": ach / peak32, "avg_ms": avg},
+            **({} if "fp64" not in lg else {"fp64_paths": large_fp64_summary(lg)})}
+
+
+def large_fp64_summary(lg):
+    """The large case stepped in FP64, plain and begun in FP32 (2 timed
+    steps each after 1 warm-up): step times at the FP64 energy drift."""
+    out = {}
+    for k in ("fp64", "fp32_first"):
+        r = lg[k]
+        out[k] = {"ms_per_step": r["ms"] / r["steps"], "max_abs_rel_dE": r["drift"],
+                  "mean_map_evals_per_step": statistics.mean(r["evals"]),
+                  "mean_fp32_evals_per_step": statistics.mean(r["fp32_evals"]),
+                  "value": r["pushes"] / (r["ms"] * 1e-3)}
+    out["fp32_first_step_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / \
+        out["fp32_first"]["ms_per_step"]
+    out["mixed_step_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / (lg["ms"] / lg["steps"])
+    return out
 
 
 # ---------------------------------------------------------------- our arm
@@ -478,14 +506,14 @@ def run_ours(args):
     if args.only == "large":
         lg = run_large(args, rank, barrier, flush, stream)
         print(json.dumps({"profile_run": "large", "ms": lg["ms"], "pushes": lg["pushes"],
-                          "stats": lg["stats"]}), flush=True)
+                          "stats": lg["stats"]}, default=_json_default), flush=True)
         return
     if args.only == "ensemble":
         ens, ntot = run_ensemble(args, rank, barrier, flush, stream)
         for label, r in ens.items():
             print(json.dumps({"profile_run": f"ensemble_{label}", "ms": r["ms"],
                               "pushes": r["pushes"], "particles": ntot,
-                              "stats": r.get("stats")}), flush=True)
+                              "stats": r.get("stats")}, default=_json_default), flush=True)
         return
 
     results = {}
@@ -529,7 +557,7 @@ def run_ours(args):
         # profiling invocation: a short run of one path, no report line
         for label, r in results.items():
             print(json.dumps({"profile_run": label, "ms": r["ms"], "pushes": r["pushes"],
-                              "stats": r["stats"]}), flush=True)
+                              "stats": r["stats"]}, default=_json_default), flush=True)
         if dist:
             dist.destroy_process_group()
         return
@@ -662,7 +690,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline_subprocess(args)
     if rank == 0:
-        print(json.dumps(out), flush=True)
+        print(json.dumps(out, default=_json_default), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -843,7 +871,14 @@ def run_reference(args):
                       "note": "FP64 CPU oracle on a bounded particle sample of the workload"},
            "cpu_baseline": cb,
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(out), flush=True)
+    print(json.dumps(out, default=_json_default), flush=True)
+
+
+def _json_default(o):
+    """numpy scalars (counters read back from the library) as Python numbers."""
+    if hasattr(o, "item"):
+        return o.item()
+    raise TypeError(f"not JSON serialisable: {type(o).__name__}")
 
 
 def main():
@@ -856,19 +891,21 @@ def main():
     ap.add_argument("--only", choices=["fp64", "mixed", "ensemble", "large"], default=None,
                     help="profiling run of one path (prints no report line)")
     ap.add_argument("--no-large", action="store_true", help="skip the 67M-particle case")
+    ap.add_argument("--no-large-fp64", action="store_true",
+                    help="skip the FP64 steps of the 67M-particle case")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling run without the e2e arm")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sample-one", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sample-1d", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_sample_1d:
-        print(json.dumps(oracle_two_stream_run()), flush=True)
+        print(json.dumps(oracle_two_stream_run(), default=_json_default), flush=True)
         return
     if args.cpu_sample:
-        print(json.dumps(oracle_sample()), flush=True)
+        print(json.dumps(oracle_sample(), default=_json_default), flush=True)
         return
     if args.cpu_sample_one:
-        print(json.dumps(oracle_one_map_evaluation()), flush=True)
+        print(json.dumps(oracle_one_map_evaluation(), default=_json_default), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

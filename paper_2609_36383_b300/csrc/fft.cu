@@ -18,36 +18,41 @@ namespace {
 constexpr int kFftThreads = 256;
 constexpr int kFftSmemElems = 4096;  // double2 per CTA (64 KB)
 
+// Every size here is a power of two (line length N = 2^logN, the stride of
+// the axis 2^logS, lines per CTA), so the index arithmetic uses shifts and
+// masks rather than integer divisions.
 __global__ void __launch_bounds__(kFftThreads)
-k_fft_axis(double2 *__restrict__ data, int Ng, int N, int logN, int stride, int lines,
-           int lpb, const double2 *__restrict__ tw, int inverse) {
+k_fft_axis(double2 *__restrict__ data, int Ng, int N, int logN, int logS, int lines, int lpb,
+           int loglpb, const double2 *__restrict__ tw, int inverse) {
   extern __shared__ double2 sm[];
   double2 *base_data = data + (size_t)blockIdx.y * Ng;
   const int line0 = blockIdx.x * lpb;
   const int nl = min(lpb, lines - line0);
   const int tot = nl * N;
+  const int smask = (1 << logS) - 1, nmask = N - 1;
   // load, bit-reversed within each line
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
     int b, k;
-    if (stride == 1) { b = t / N; k = t - b * N; }
-    else { k = t / nl; b = t - k * nl; }
-    int ln = line0 + b;
-    int inner = ln % stride, outer = ln / stride;
-    size_t addr = (size_t)inner + (size_t)outer * stride * N + (size_t)k * stride;
-    int kr = (int)(__brev((unsigned)k) >> (32 - logN));
-    sm[b * N + kr] = base_data[addr];
+    if (logS == 0) { b = t >> logN; k = t & nmask; }
+    else { k = t >> loglpb; b = t & (lpb - 1); }
+    const int ln = line0 + b;
+    const int inner = ln & smask, outer = ln >> logS;
+    const size_t addr = (size_t)inner + ((size_t)outer << (logS + logN)) + ((size_t)k << logS);
+    const int kr = (int)(__brev((unsigned)k) >> (32 - logN));
+    sm[(b << logN) + kr] = base_data[addr];
   }
   __syncthreads();
-  const int half = N >> 1;
-  for (int h = 1; h < N; h <<= 1) {
-    const int tstep = N / (2 * h);
-    for (int t = threadIdx.x; t < nl * half; t += blockDim.x) {
-      int b = t / half, j = t - b * half;
-      int grp = j / h, pos = j - grp * h;
-      int i0 = b * N + grp * 2 * h + pos, i1 = i0 + h;
-      double2 wv = tw[pos * tstep];
+  const int logHalf = logN - 1;
+  for (int lh = 0; lh < logN; lh++) {
+    const int h = 1 << lh;
+    const int tshift = logN - 1 - lh;  // twiddle stride N / (2h)
+    for (int t = threadIdx.x; t < (nl << logHalf); t += blockDim.x) {
+      const int b = t >> logHalf, j = t & ((1 << logHalf) - 1);
+      const int grp = j >> lh, pos = j & (h - 1);
+      const int i0 = (b << logN) + (grp << (lh + 1)) + pos, i1 = i0 + h;
+      double2 wv = tw[pos << tshift];
       if (inverse) wv.y = -wv.y;
-      double2 x0 = sm[i0], x1 = sm[i1];
+      const double2 x0 = sm[i0], x1 = sm[i1];
       double2 y;
       y.x = wv.x * x1.x - wv.y * x1.y;
       y.y = wv.x * x1.y + wv.y * x1.x;
@@ -58,12 +63,12 @@ k_fft_axis(double2 *__restrict__ data, int Ng, int N, int logN, int stride, int 
   }
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
     int b, k;
-    if (stride == 1) { b = t / N; k = t - b * N; }
-    else { k = t / nl; b = t - k * nl; }
-    int ln = line0 + b;
-    int inner = ln % stride, outer = ln / stride;
-    size_t addr = (size_t)inner + (size_t)outer * stride * N + (size_t)k * stride;
-    base_data[addr] = sm[b * N + k];
+    if (logS == 0) { b = t >> logN; k = t & nmask; }
+    else { k = t >> loglpb; b = t & (lpb - 1); }
+    const int ln = line0 + b;
+    const int inner = ln & smask, outer = ln >> logS;
+    const size_t addr = (size_t)inner + ((size_t)outer << (logS + logN)) + ((size_t)k << logS);
+    base_data[addr] = sm[(b << logN) + k];
   }
 }
 
@@ -120,8 +125,11 @@ int fft_nd(pic_ctx *ctx, double2 *data, int batch, int sign) {
     threads = threads < 32 ? 32 : (threads > kFftThreads ? kFftThreads : (threads + 31) / 32 * 32);
     dim3 grid((lines + lpb - 1) / lpb, batch);
     size_t smem = sizeof(double2) * (size_t)lpb * N;
-    k_fft_axis<<<grid, threads, smem, ctx->st>>>(data, g.Ng, N, g.logn[a], stride, lines, lpb,
-                                                 ctx->tw[a], sign > 0 ? 1 : 0);
+    int logS = 0, loglpb = 0;
+    while ((1 << logS) < stride) logS++;
+    while ((1 << loglpb) < lpb) loglpb++;
+    k_fft_axis<<<grid, threads, smem, ctx->st>>>(data, g.Ng, N, g.logn[a], logS, lines, lpb,
+                                                 loglpb, ctx->tw[a], sign > 0 ? 1 : 0);
     KCHECK();
     stride *= N;
   }

@@ -283,6 +283,39 @@ def test_tsi_full_run_matches_printed_diagnostics(dt, key):
     assert dE < 1e-11
 
 
+def test_wbi02_residuals_to_t20():
+    """Sec. 5.2: WBI-0.2 to t = 20 (100 steps, the first fifth of the run
+    below), with every step's Gauss and Lorenz RMS residuals, |dE/E|, the
+    chain-rule residual R_A and the work residual within ten times the
+    maxima the paper prints for the whole run (5.12e-13, 3.95e-14, 4.13e-13,
+    5.57e-16, 1.31e-13), and the final-evaluation inner counts reported beside
+    the paper's run mean 5.038 (maximum 8)."""
+    from oracle import closed_form as cf
+    G = cf.weibel_rate(1.0, 0.9, math.pi / 16)
+    cfg = pic_inputs.weibel_3d(eigen_rate=G, eigen_chi=cf.chi(1.0, math.pi / 16), dt=0.2)
+    s = make_gpu(cfg, inner_tol_scale=0.1)  # Table 1: WBI inner tolerances 10x tighter
+    s.start()
+    printed = dict(gauss=5.12e-13, lorenz=3.95e-14, dE=4.13e-13, chain=5.57e-16, work=1.31e-13)
+    mx = dict(gauss=0.0, lorenz=0.0, dE=0.0, chain=0.0, work=0.0)
+    inner, inner_max, outer = [], 0, []
+    for _ in range(100):
+        r = s.step(cfg["tol"])
+        assert r["status"] == 0
+        mx["gauss"] = max(mx["gauss"], r["gauss_rms"])
+        mx["lorenz"] = max(mx["lorenz"], r["lorenz_rms"])
+        mx["dE"] = max(mx["dE"], abs(r["rel_dE"]))
+        mx["chain"] = max(mx["chain"], r["chain_rms"])
+        mx["work"] = max(mx["work"], abs(r["work_residual"]))
+        inner.append(r["inner_mean"])
+        inner_max = max(inner_max, r["inner_max"])
+        outer.append(r["outer_iters"])
+    print("WBI-0.2 to t = 20: " + ", ".join(f"max {k} {v:.2e}" for k, v in mx.items())
+          + f"; inner mean {np.mean(inner):.3f} max {inner_max}; outer mean {np.mean(outer):.3f}")
+    for k, v in mx.items():
+        assert v <= 10 * printed[k], k
+    s.close()
+
+
 @pytest.mark.skipif(os.environ.get("PIC_LONG_RUNS") != "1",
                     reason="2500- and 500-step 3D runs (WBI-0.04 alone about 30 minutes); "
                            "set PIC_LONG_RUNS=1")
