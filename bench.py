@@ -210,6 +210,7 @@ def run_ensemble(args, rank, barrier, flush, stream):
     nps = [c["w"].shape[0] for c in cfgs]
 
     failed = {"n": 0}
+    hc = dict(host_control=1) if args.host_control else {}
 
     def timed(step_fn, nsteps):
         ms, pushes, drift, evals = 0.0, 0, 0.0, []
@@ -235,7 +236,7 @@ def run_ensemble(args, rank, barrier, flush, stream):
 
     out = {}
     for label, prec in (("mixed", P.PIC_MIXED), ("fp64", P.PIC_FP64)):
-        bt = P.batch_from_configs(cfgs, precision=prec, sort_every=10)
+        bt = P.batch_from_configs(cfgs, precision=prec, sort_every=10, **hc)
         bt.start()
         for _ in range(args.warmup):
             bt.step(tol)
@@ -250,7 +251,7 @@ def run_ensemble(args, rank, barrier, flush, stream):
         failed["n"] = 0
     if args.only != "ensemble":
         # the plain FP64 path: one context per instance, stepped in turn
-        sims = [P.from_config(c, precision=P.PIC_FP64) for c in cfgs]
+        sims = [P.from_config(c, precision=P.PIC_FP64, **hc) for c in cfgs]
         for s in sims:
             s.start()
         for _ in range(args.warmup):
@@ -404,8 +405,10 @@ def run_large(args, rank, barrier, flush, stream):
     cfg = pic_inputs.weibel_2d_ions(seed=rank)
     npart = cfg["w"].shape[0]
 
+    hc = dict(host_control=1) if args.host_control else {}
+
     def run(precision, warmup, steps, **opts):
-        sim = P.from_config(cfg, precision=precision, sort_every=10, **opts)
+        sim = P.from_config(cfg, precision=precision, sort_every=10, **hc, **opts)
         sim.start()
         for _ in range(warmup):
             step_retrying(sim, cfg["tol"], npart)
@@ -436,7 +439,8 @@ def run_large(args, rank, barrier, flush, stream):
         # FP64 steps of the same case (about 11 GB of FP64 particle state), plain
         # and begun in FP32: the mixed path's speed at the FP64 energy drift
         out["fp64"] = run(P.PIC_FP64, 1, 2)
-        out["fp32_first"] = run(P.PIC_FP64, 1, 2, fp32_first=1)
+        if not args.host_control:
+            out["fp32_first"] = run(P.PIC_FP64, 1, 2, fp32_first=1)
     return out
 
 
@@ -538,6 +542,9 @@ def run_ours(args):
              ("fp32_first", P.PIC_FP64, dict(fp32_first=1)))
     if args.only:
         paths = tuple(p for p in paths if p[0] == args.only)
+    if args.host_control:  # the FP32-first stage exists under device control only
+        paths = tuple((lb, pr, dict(po, host_control=1)) for lb, pr, po in paths
+                      if not po.get("fp32_first"))
     # one clock sampler spans both timed regions (the mixed one alone is far
     # shorter than nvidia-smi's sampling interval)
     clk = ClockSampler(local).__enter__()
@@ -907,10 +914,16 @@ def main():
     ap.add_argument("--no-large-fp64", action="store_true",
                     help="skip the FP64 steps of the 67M-particle case")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling run without the e2e arm")
+    ap.add_argument("--host-control", action="store_true",
+                    help="profiling run: Algorithm 1's decisions taken on the host, so that "
+                         "every kernel launches outside conditional graph nodes (which a "
+                         "per-kernel profiler cannot capture)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sample-one", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sample-1d", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.host_control and not args.only:
+        ap.error("--host-control is for the --only profiling runs")
     if args.cpu_sample_1d:
         print(json.dumps(oracle_two_stream_run(), default=_json_default), flush=True)
         return

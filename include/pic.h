@@ -125,7 +125,9 @@ typedef struct {
                                    device, and a step's whole outer iteration runs as two
                                    CUDA graph launches with one synchronisation at the
                                    end; 1: the host takes them, synchronising after every
-                                   map evaluation (the same decisions, for checks) */
+                                   map evaluation (the same decisions, for checks).  In a
+                                   batch, 1 likewise has the host launch each round and
+                                   read the loop state after it */
   int nonlinear_solver;         /* PIC_SOLVER_ANDERSON (default): Algorithm 1's type-II
                                    Anderson iteration; PIC_SOLVER_NEWTON_KRYLOV: inexact
                                    Newton on H(j) - j = 0, each direction from

@@ -1381,7 +1381,8 @@ int b_rounds(pic_batch *bt, double tr, double ta, double itr, double ita) {
   if (bt->graph_ok == 1 && (bt->graph_tr != tr || bt->graph_ta != ta || bt->graph_itr != itr ||
                             bt->graph_ita != ita))
     bt->graph_ok = 0;
-  if (bt->graph_ok == 0) bt->graph_ok = build_loop_graph(bt, tr, ta, itr, ita) ? 1 : -1;
+  if (bt->graph_ok == 0)
+    bt->graph_ok = !bt->opt.host_control && build_loop_graph(bt, tr, ta, itr, ita) ? 1 : -1;
   if (bt->graph_ok == 1) {
     BCK(cudaGraphLaunch(bt->loop_exec, bt->st));
     return PIC_OK;  // launches are counted from the rounds the loop reports
