@@ -76,6 +76,7 @@ struct KConst {
   int order;       // shape degree (2, or 1)
   int refine_max;  // convergence-triggered refinement depth (0 = off)
   double qs[PIC_MAX_SPECIES], ms[PIC_MAX_SPECIES];
+  T qT[PIC_MAX_SPECIES], mT[PIC_MAX_SPECIES];  // the same in the particle real type
 };
 
 // Mesh scales of one problem in the particle real type, kept apart from
@@ -108,6 +109,8 @@ KConst<T> kconst(const StepConst &sc, const PGeom &pg) {
   for (int s = 0; s < PIC_MAX_SPECIES; s++) {
     k.qs[s] = sc.qs[s];
     k.ms[s] = sc.ms[s];
+    k.qT[s] = (T)sc.qs[s];
+    k.mT[s] = (T)sc.ms[s];
   }
   return k;
 }
@@ -326,17 +329,83 @@ struct PieceAcc {
   T W1[D][NN];
 };
 
+// One Gauss-Legendre point (s, weight wt) of a piece's orbit integrals;
+// FIRST assigns the point's terms (the piece's first point) instead of
+// adding them, so the accumulators need no clearing.
+template <bool FIRST, typename T>
+__device__ __forceinline__ void acc_put(T &x, T v) {
+  if (FIRST) x = v;
+  else x += v;
+}
+
+template <int D, typename T, bool DERIV, bool FIRST>
+__device__ __forceinline__ void piece_point(const T t0[3], const bool pos[3], bool lin,
+                                            const T del[3], T s, T wt, PieceAcc<D, T> &pa) {
+  T S[3][3], dS[3][3];
+#pragma unroll
+  for (int l = 0; l < D; l++) {
+    if (lin) lspline<T>(t0[l] + s * del[l], pos[l], S[l], dS[l]);
+    else qspline<T>(t0[l] + s * del[l], S[l], dS[l]);
+  }
+  if (D == 1) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      acc_put<FIRST>(pa.Sb[i], wt * S[0][i]);
+      if (DERIV) {
+        T b = wt * dS[0][i];
+        acc_put<FIRST>(pa.Wd[0][i], b);
+        acc_put<FIRST>(pa.W1[0][i], s * b);
+      }
+    }
+  } else if (D == 2) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      const T a = wt * S[0][i];
+      const T b = wt * dS[0][i];
+      const T c = s * a, e = s * b;
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        const int k = i + 3 * j;
+        acc_put<FIRST>(pa.Sb[k], a * S[1][j]);
+        if (DERIV) {
+          acc_put<FIRST>(pa.Wd[0][k], b * S[1][j]);
+          acc_put<FIRST>(pa.W1[0][k], e * S[1][j]);
+          acc_put<FIRST>(pa.Wd[D > 1 ? 1 : 0][k], a * dS[1][j]);
+          acc_put<FIRST>(pa.W1[D > 1 ? 1 : 0][k], c * dS[1][j]);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+      for (int j = 0; j < 3; j++) {
+        const T ab = wt * S[0][i] * S[1][j];
+        const T dab = wt * dS[0][i] * S[1][j];
+        const T adb = wt * S[0][i] * dS[1][j];
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+          const int k = i + 3 * (j + 3 * l);
+          acc_put<FIRST>(pa.Sb[k], ab * S[2][l]);
+          if (DERIV) {
+            const T d0 = dab * S[2][l], d1 = adb * S[2][l], d2 = ab * dS[2][l];
+            acc_put<FIRST>(pa.Wd[0][k], d0);
+            acc_put<FIRST>(pa.W1[0][k], s * d0);
+            acc_put<FIRST>(pa.Wd[D > 1 ? 1 : 0][k], d1);
+            acc_put<FIRST>(pa.W1[D > 1 ? 1 : 0][k], s * d1);
+            acc_put<FIRST>(pa.Wd[D > 2 ? 2 : 0][k], d2);
+            acc_put<FIRST>(pa.W1[D > 2 ? 2 : 0][k], s * d2);
+          }
+        }
+      }
+  }
+}
+
+// The orbit integrals of one piece over its kc.ngl Gauss-Legendre points.
 template <int D, typename T, bool DERIV>
 __device__ __forceinline__ void accumulate_piece(const KConst<T> &kc, const T off[3],
                                                  const T del[3], const int base[3], T sa, T sb,
                                                  PieceAcc<D, T> &pa, int order) {
-  constexpr int NN = PieceAcc<D, T>::NN;
-#pragma unroll
-  for (int k = 0; k < NN; k++) {
-    pa.Sb[k] = T(0);
-#pragma unroll
-    for (int j = 0; j < D; j++) pa.Wd[j][k] = pa.W1[j][k] = T(0);
-  }
   const T len = sb - sa;
   T t0[3];
   bool pos[3] = {false, false, false};
@@ -346,69 +415,36 @@ __device__ __forceinline__ void accumulate_piece(const KConst<T> &kc, const T of
     t0[l] = off[l] - T(base[l]);
     if (lin) pos[l] = t0[l] + T(0.5) * (sa + sb) * del[l] >= T(0);
   }
+  if constexpr (!std::is_same<T, float>::value) {
+    // FP64 (and dual numbers): cleared accumulators and a rolled point loop,
+    // the smaller code for a kernel bound by the FP64 pipe
+    constexpr int NN = PieceAcc<D, T>::NN;
+#pragma unroll
+    for (int k = 0; k < NN; k++) {
+      pa.Sb[k] = T(0);
+#pragma unroll
+      for (int j = 0; j < D; j++) pa.Wd[j][k] = pa.W1[j][k] = T(0);
+    }
 #pragma unroll 1
-  for (int qp = 0; qp < kc.ngl; qp++) {
-    const T s = sa + len * kc.gl_t[qp];
-    const T wt = len * kc.gl_w[qp];
-    T S[3][3], dS[3][3];
-#pragma unroll
-    for (int l = 0; l < D; l++) {
-      if (lin) lspline<T>(t0[l] + s * del[l], pos[l], S[l], dS[l]);
-      else qspline<T>(t0[l] + s * del[l], S[l], dS[l]);
-    }
-    if (D == 1) {
-#pragma unroll
-      for (int i = 0; i < 3; i++) {
-        pa.Sb[i] += wt * S[0][i];
-        if (DERIV) {
-          T b = wt * dS[0][i];
-          pa.Wd[0][i] += b;
-          pa.W1[0][i] += s * b;
-        }
-      }
-    } else if (D == 2) {
-#pragma unroll
-      for (int i = 0; i < 3; i++) {
-        const T a = wt * S[0][i];
-        const T b = wt * dS[0][i];
-        const T c = s * a, e = s * b;
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-          const int k = i + 3 * j;
-          pa.Sb[k] += a * S[1][j];
-          if (DERIV) {
-            pa.Wd[0][k] += b * S[1][j];
-            pa.W1[0][k] += e * S[1][j];
-            pa.Wd[D > 1 ? 1 : 0][k] += a * dS[1][j];
-            pa.W1[D > 1 ? 1 : 0][k] += c * dS[1][j];
-          }
-        }
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-          const T ab = wt * S[0][i] * S[1][j];
-          const T dab = wt * dS[0][i] * S[1][j];
-          const T adb = wt * S[0][i] * dS[1][j];
-#pragma unroll
-          for (int l = 0; l < 3; l++) {
-            const int k = i + 3 * (j + 3 * l);
-            pa.Sb[k] += ab * S[2][l];
-            if (DERIV) {
-              const T d0 = dab * S[2][l], d1 = adb * S[2][l], d2 = ab * dS[2][l];
-              pa.Wd[0][k] += d0;
-              pa.W1[0][k] += s * d0;
-              pa.Wd[D > 1 ? 1 : 0][k] += d1;
-              pa.W1[D > 1 ? 1 : 0][k] += s * d1;
-              pa.Wd[D > 2 ? 2 : 0][k] += d2;
-              pa.W1[D > 2 ? 2 : 0][k] += s * d2;
-            }
-          }
-        }
-    }
+    for (int qp = 0; qp < kc.ngl; qp++)
+      piece_point<D, T, DERIV, false>(t0, pos, lin, del, sa + len * kc.gl_t[qp],
+                                      len * kc.gl_w[qp], pa);
+    return;
   }
+  // FP32: the first point assigns (no clearing); without derivatives and
+  // with the default rule the point loop is unrolled
+  piece_point<D, T, DERIV, true>(t0, pos, lin, del, sa + len * kc.gl_t[0], len * kc.gl_w[0], pa);
+  if (!DERIV && kc.ngl == D + 1) {
+#pragma unroll
+    for (int qp = 1; qp < D + 1; qp++)
+      piece_point<D, T, DERIV, false>(t0, pos, lin, del, sa + len * kc.gl_t[qp],
+                                      len * kc.gl_w[qp], pa);
+    return;
+  }
+#pragma unroll 1
+  for (int qp = 1; qp < kc.ngl; qp++)
+    piece_point<D, T, DERIV, false>(t0, pos, lin, del, sa + len * kc.gl_t[qp], len * kc.gl_w[qp],
+                                    pa);
 }
 
 // 3D: the same orbit integrals for the 9 nodes (ox, oy) of one z-slab oz of
@@ -629,21 +665,15 @@ struct DepositOrbit {
     }
     PieceAcc<D, T> pa;
     accumulate_piece<D, T, FINAL>(*kc, off, del, base, sa, sb, pa, order);
-    // window coordinates of the piece's base node (relative to ref)
-    int wx = 0, wy = 0;
-    if (WarpWin<D>::kOn && win) {
-      wx = wrap_rel(cell[0] + base[0] - ref[0], pg->n[0]) - 1 - WarpWin<D>::LO0;
-      wy = D > 1 ? wrap_rel(cell[1] + base[1] - ref[1], pg->n[1]) - 1 - WarpWin<D>::LO1 : 0;
-    }
+    if (FINAL) {
 #pragma unroll
-    for (int oz = 0; oz < (D > 2 ? 3 : 1); oz++)
+      for (int oz = 0; oz < (D > 2 ? 3 : 1); oz++)
 #pragma unroll
-      for (int oy = 0; oy < (D > 1 ? 3 : 1); oy++)
+        for (int oy = 0; oy < (D > 1 ? 3 : 1); oy++)
 #pragma unroll
-        for (int ox = 0; ox < 3; ox++) {
-          const int k = ox + 3 * (oy + 3 * oz);
-          const int g = nr.at(ox, oy, oz);
-          if (FINAL) {
+          for (int ox = 0; ox < 3; ox++) {
+            const int k = ox + 3 * (oy + 3 * oz);
+            const int g = nr.at(ox, oy, oz);
             T r[NVP], u[4];
             load_rec<NVP>(nodes + (size_t)g * NVP, r);
             load_rec<4>(nodes_u + (size_t)g * 4, u);
@@ -661,6 +691,36 @@ struct DepositOrbit {
               for (int j = 0; j < D; j++) Dm[c][j] += An * pa.Wd[j][k] + dA * pa.W1[j][k];
             }
           }
+    }
+    // window coordinates of the piece's base node (relative to ref)
+    int wx = -1, wy = -1;
+    if (WarpWin<D>::kOn && win) {
+      wx = wrap_rel(cell[0] + base[0] - ref[0], pg->n[0]) - 1 - WarpWin<D>::LO0;
+      wy = D > 1 ? wrap_rel(cell[1] + base[1] - ref[1], pg->n[1]) - 1 - WarpWin<D>::LO1 : 0;
+    }
+    if (WarpWin<D>::kOn && win && wx >= 0 && wx + 2 < WarpWin<D>::N0 && wy >= 0 &&
+        wy + (D > 1 ? 2 : 0) < WarpWin<D>::N1) {
+      // the piece's whole stencil lies in the window: fixed offsets from one base
+      T *w0 = win + (size_t)3 * (wx + WarpWin<D>::N0 * wy) * 32;
+#pragma unroll
+      for (int oy = 0; oy < (D > 1 ? 3 : 1); oy++)
+#pragma unroll
+        for (int ox = 0; ox < 3; ox++) {
+          const int k = ox + 3 * oy;
+#pragma unroll
+          for (int c = 0; c < 3; c++)
+            w0[(3 * (ox + WarpWin<D>::N0 * oy) + c) * 32] += qv[c] * pa.Sb[k];
+        }
+      return;
+    }
+#pragma unroll
+    for (int oz = 0; oz < (D > 2 ? 3 : 1); oz++)
+#pragma unroll
+      for (int oy = 0; oy < (D > 1 ? 3 : 1); oy++)
+#pragma unroll
+        for (int ox = 0; ox < 3; ox++) {
+          const int k = ox + 3 * (oy + 3 * oz);
+          const int g = nr.at(ox, oy, oz);
           int e = -1;
           if (WarpWin<D>::kOn && win) {
             const int rx = wx + ox, ry = wy + (D > 1 ? oy : 0);
@@ -1354,16 +1414,17 @@ __device__ __forceinline__ void map_block(const PView<S> &pv, const int64_t i_sl
 //
 // A warp executes each inner sweep for as long as its slowest lane still
 // iterates, so in map_block the lanes whose particles converged early idle
-// until the warp's last particle converges.  map_chunk removes that wait: a
-// CTA owns a chunk of kRefill * kPT particles, and a lane whose particle has
-// converged (or failed) stores it and takes the next particle of the chunk
-// from a shared counter, so the sweeps run with full warps until the chunk
-// runs dry.  The chunk is ordered by the predicted number of knot planes
-// crossed (as in map_block) so that the particles a warp holds at one time
-// walk similar numbers of orbit pieces.  The deposits follow in a second
-// phase, over the chunk in that order, from the stored orbit velocities.
-// Every particle's arithmetic is that of map_block: only which lane
-// computes it, and when, changes.
+// until the warp's last particle converges.  map_chunk_solve removes that
+// wait: a CTA owns a chunk of kRefill * kPT particles, and a lane whose
+// particle has converged (or failed) stores it and takes the next particle of
+// the chunk from a shared counter, so the sweeps run with full warps until
+// the chunk runs dry.  The chunk is ordered by the predicted number of knot
+// planes crossed (as in map_block) so that the particles a warp holds at one
+// time walk similar numbers of orbit pieces.  The deposits follow from the
+// stored orbit velocities (map_chunk_deposit): in a second launch for FP32
+// arithmetic (k_map_solve, k_map_deposit), in the same CTA after a barrier
+// for FP64 (k_map_fused).  Every particle's arithmetic is that of map_block:
+// only which lane computes it, and when, changes.
 constexpr int kRefill = 4;
 constexpr int kChunk = kRefill * kPT;
 
@@ -1382,8 +1443,16 @@ __device__ __forceinline__ void lane_init(LaneSolve<D, T> &ls, const PView<S> &p
   const int64_t cap = pv.cap;
   const int s_id = pv.sp[i];
   PushConst<T> &pc = ls.pc;
-  pc.q = (T)(pv.w[i] * kc.qs[s_id]);
-  pc.m = (T)(pv.w[i] * kc.ms[s_id]);
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32: the weight rounded once, then FP32 products (no FP64 arithmetic,
+    // whose pipe is 1/64 of the FP32 one)
+    const float wf = (float)pv.w[i];
+    pc.q = wf * kc.qT[s_id];
+    pc.m = wf * kc.mT[s_id];
+  } else {
+    pc.q = (T)(pv.w[i] * kc.qs[s_id]);
+    pc.m = (T)(pv.w[i] * kc.ms[s_id]);
+  }
   const T kap = kc.kappa, dt = kc.dt;
   pc.inv_m = T(1) / pc.m;
   pc.mk = pc.m * kap;
@@ -1455,23 +1524,15 @@ __device__ __forceinline__ int lane_sweep(LaneSolve<D, T> &ls, const T *__restri
   return 0;
 }
 
-// The particle map over one chunk of kChunk particle slots starting at c0
-// (the common path: quadratic shapes, no refinement).  psum[0..2) receives
-// the CTA's final-pass partial sums.
-template <int D, typename T, bool FINAL, typename S>
-__device__ __forceinline__ void map_chunk(const PView<S> &pv, const int64_t c0,
-                                          const T *__restrict__ nodes,
-                                          const T *__restrict__ nodes_u, double *__restrict__ J,
-                                          const PGeom &pg, const KConst<T> &kc,
-                                          const MapScale<T> &ms, EvalCounters *__restrict__ cnt,
-                                          double *__restrict__ psum) {
-  __shared__ int s_order[kChunk];
+// Orders the nvalid particles of the chunk at c0 by the number of knot
+// planes (0, 1, 2 or more) that a straight orbit with velocity vel crosses
+// (stable, deterministic), into s_order.  Ends with a barrier.
+template <int D, typename T, typename S>
+__device__ __forceinline__ void order_chunk(const PView<S> &pv, const int64_t c0, int nvalid,
+                                            const S *__restrict__ vel, const KConst<T> &kc,
+                                            const MapScale<T> &ms, int *s_order) {
   __shared__ int s_wcnt[kRefill][kPT / 32][4];
-  __shared__ int s_next;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t nvalid64 = pv.np - c0;
-  const int nvalid = nvalid64 < kChunk ? (int)nvalid64 : kChunk;
-  // 1. order the chunk by predicted crossing class (stable, deterministic)
   int cls_of[kRefill];
   unsigned mine[kRefill];
 #pragma unroll
@@ -1483,9 +1544,7 @@ __device__ __forceinline__ void map_chunk(const PView<S> &pv, const int64_t c0,
       cls = 0;
 #pragma unroll
       for (int l = 0; l < D; l++) {
-        const T u = (T)pv.off[l * pv.cap + i] +
-                    (T)(kc.warm ? pv.vbar[l * pv.cap + i] : pv.v0[l * pv.cap + i]) * kc.dt *
-                        ms.inv_dx[l];
+        const T u = (T)pv.off[l * pv.cap + i] + (T)vel[l * pv.cap + i] * kc.dt * ms.inv_dx[l];
         cls += (u >= T(0.5) || u < T(-0.5)) ? 1 : 0;
       }
       cls = cls < 2 ? cls : 2;
@@ -1499,7 +1558,6 @@ __device__ __forceinline__ void map_chunk(const PView<S> &pv, const int64_t c0,
       if (cls == c) mine[q] = b;
     }
   }
-  if (threadIdx.x == 0) s_next = 0;
   __syncthreads();
 #pragma unroll
   for (int q = 0; q < kRefill; q++) {
@@ -1514,6 +1572,24 @@ __device__ __forceinline__ void map_chunk(const PView<S> &pv, const int64_t c0,
     s_order[pos] = q * kPT + threadIdx.x;
   }
   __syncthreads();
+}
+
+// The inner solves of the particle map over one chunk of kChunk particle
+// slots starting at c0 (the common path: quadratic shapes, no refinement):
+// every particle's orbit velocity, P^{n+1} and inner count (-1 on failure)
+// are stored for the deposit pass (map_chunk_deposit).
+template <int D, typename T, typename S>
+__device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_t c0,
+                                                const T *__restrict__ nodes, const PGeom &pg,
+                                                const KConst<T> &kc, const MapScale<T> &ms,
+                                                EvalCounters *__restrict__ cnt, int *s_order) {
+  __shared__ int s_next;
+  const int lane = threadIdx.x & 31;
+  const int64_t nvalid64 = pv.np - c0;
+  const int nvalid = nvalid64 < kChunk ? (int)nvalid64 : kChunk;
+  if (threadIdx.x == 0) s_next = 0;
+  // 1. order the chunk by predicted crossing class
+  order_chunk<D, T, S>(pv, c0, nvalid, kc.warm ? pv.vbar : pv.v0, kc, ms, s_order);
   // 2. the inner solves, lanes refilled from the chunk
   int npieces = 0, mx_it = 0;
   unsigned it_sum = 0;
@@ -1550,55 +1626,6 @@ __device__ __forceinline__ void map_chunk(const PView<S> &pv, const int64_t c0,
       }
     }
   }
-  __syncthreads();  // every orbit velocity of the chunk stored
-  // 3. the deposits, in class order, kPT particles at a time
-  double work = 0.0, chain = 0.0;
-  constexpr bool kWin = WarpWin<D>::kOn && sizeof(T) == 4;
-  __shared__ T s_win[kWin ? (kPT / 32) * WarpWin<D>::NE * 32 : 1];
-  T *win_warp = s_win + (size_t)wid * WarpWin<D>::NE * 32;
-  T *win_col = kWin ? win_warp + lane : nullptr;
-#pragma unroll 1
-  for (int q = 0; q < kRefill; q++) {
-    const int kk = q * kPT + threadIdx.x;
-    const int64_t ip = kk < nvalid ? c0 + s_order[kk] : -1;
-    const bool act = ip >= 0 && pv.iters[ip] > 0;
-    int ref[3] = {0, 0, 0};
-    if constexpr (kWin) {
-      const int64_t i0 = __shfl_sync(0xffffffffu, ip, 0);
-      if (i0 >= 0) {
-#pragma unroll
-        for (int l = 0; l < D; l++) ref[l] = pv.cell[l * pv.cap + i0];
-      }
-      for (int e = 0; e < WarpWin<D>::NE; e++) win_col[e * 32] = T(0);
-    }
-    if (act) {
-      LaneSolve<D, T> d;
-      lane_init<D, T, S>(d, pv, ip, kc, ms);
-#pragma unroll
-      for (int c = 0; c < 3; c++) d.vb[c] = (T)pv.vbar[c * pv.cap + ip];
-      deposit_orbit<D, T, FINAL, false>(d.pc, d.cell, d.off, d.dtdx, T(0), T(1), kc.dt, T(1),
-                                        d.vb, nodes, nodes_u, J, pg, kc, ms, win_col, ref,
-                                        npieces, st, work, chain, 2);
-    }
-    if constexpr (kWin) {
-      __syncwarp();
-      for (int e = lane; e < WarpWin<D>::NE; e += 32) {
-        const T *rowp = win_warp + (size_t)e * 32;
-        T sum = T(0);
-#pragma unroll 8
-        for (int l = 0; l < 32; l++) sum += rowp[(l + lane) & 31];
-        if (sum != T(0)) {
-          const int node = e / 3, c = e - 3 * node;
-          const int rx = node % WarpWin<D>::N0 + WarpWin<D>::LO0;
-          const int ry = node / WarpWin<D>::N0 + WarpWin<D>::LO1;
-          int g = (ref[0] + rx) & pg.mask[0];
-          if (D > 1) g += pg.n0 * ((ref[1] + ry) & pg.mask[1]);
-          atomicAdd(J + (size_t)c * pg.Ng + g, widen(sum));
-        }
-      }
-      __syncwarp();
-    }
-  }
   // counters: integer warp reductions, one atomic per warp
   if (st) atomicOr(&cnt->status, st);
   const unsigned it_w = __reduce_add_sync(0xffffffffu, it_sum);
@@ -1609,6 +1636,144 @@ __device__ __forceinline__ void map_chunk(const PView<S> &pv, const int64_t c0,
     atomicAdd(&cnt->pieces, (unsigned long long)pc_w);
     if (mx > 0) atomicMax(&cnt->inner_max, mx);
   }
+}
+
+// The orbit deposits of one chunk from the stored orbit velocities (Eq.
+// orbit-current-energy), and on the final pass the particle sides of the
+// work and chain-rule sums (psum[0..2), the CTA's partials).  Lanes take the
+// particles in order of the knot planes their orbits cross, so that a warp's
+// lanes walk similar numbers of pieces.  FP32 in 1D and 2D: warp w deposits
+// the chunk slots [w R, (w + 1) R), R = kRefill * 32, ordered within that
+// range; the particles are sorted by cell, so the range lies in one or two
+// neighbouring cells, and one warp window, referenced to the range's first
+// cell, collects all kRefill rounds (cleared and summed once per chunk).
+// FP64 and 3D: the whole chunk is ordered and deposited with global atomics.
+template <int D, typename T, bool FINAL, typename S>
+__device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int64_t c0,
+                                                  const T *__restrict__ nodes,
+                                                  const T *__restrict__ nodes_u,
+                                                  double *__restrict__ J, const PGeom &pg,
+                                                  const KConst<T> &kc, const MapScale<T> &ms,
+                                                  EvalCounters *__restrict__ cnt,
+                                                  double *__restrict__ psum,
+                                                  int *s_order) {
+  constexpr int R = kRefill * 32;
+  constexpr bool kWin = WarpWin<D>::kOn && sizeof(T) == 4;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nvalid64 = pv.np - c0;
+  const int nvalid = nvalid64 < kChunk ? (int)nvalid64 : kChunk;
+  int npieces = 0;
+  unsigned int st = 0;
+  double work = 0.0, chain = 0.0;
+  if constexpr (kWin) {
+    __shared__ T s_win[(kPT / 32) * WarpWin<D>::NE * 32];
+    __shared__ short s_dord[kPT / 32][R];
+    const int r0 = wid * R;
+    int cls_q[kRefill];
+#pragma unroll
+    for (int q = 0; q < kRefill; q++) {
+      const int k = r0 + q * 32 + lane;
+      int cls = 3;  // empty slot or failed particle: last
+      if (k < nvalid && pv.iters[c0 + k] > 0) {
+        const int64_t i = c0 + k;
+        cls = 0;
+#pragma unroll
+        for (int l = 0; l < D; l++) {
+          const T u = (T)pv.off[l * pv.cap + i] + (T)pv.vbar[l * pv.cap + i] * kc.dt * ms.inv_dx[l];
+          cls += (u >= T(0.5) || u < T(-0.5)) ? 1 : 0;
+        }
+        cls = cls < 2 ? cls : 2;
+      }
+      cls_q[q] = cls;
+    }
+    // stable order by class (class, then round, then lane): the start of
+    // round q's slots of class c is warp-uniform, from the ballots' counts
+    unsigned bal[kRefill][4];
+    int start[kRefill][4];
+    int acc = 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+#pragma unroll
+      for (int q = 0; q < kRefill; q++) {
+        bal[q][c] = __ballot_sync(0xffffffffu, cls_q[q] == c);
+        start[q][c] = acc;
+        acc += __popc(bal[q][c]);
+      }
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int q = 0; q < kRefill; q++) {
+      const int c = cls_q[q];
+      const unsigned b = c == 0 ? bal[q][0] : c == 1 ? bal[q][1] : c == 2 ? bal[q][2] : bal[q][3];
+      const int s0 =
+          c == 0 ? start[q][0] : c == 1 ? start[q][1] : c == 2 ? start[q][2] : start[q][3];
+      s_dord[wid][s0 + __popc(b & lt)] = (short)(q * 32 + lane);
+    }
+    int ref[3] = {0, 0, 0};
+    if (r0 < nvalid) {
+#pragma unroll
+      for (int l = 0; l < D; l++) ref[l] = pv.cell[l * pv.cap + c0 + r0];
+    }
+    T *win_warp = s_win + (size_t)wid * WarpWin<D>::NE * 32;
+    T *win_col = win_warp + lane;
+    for (int e = 0; e < WarpWin<D>::NE; e++) win_col[e * 32] = T(0);
+    __syncwarp();
+#pragma unroll 1
+    for (int q = 0; q < kRefill; q++) {
+      const int k = r0 + s_dord[wid][q * 32 + lane];
+      const int64_t ip = c0 + k;
+      if (k < nvalid && pv.iters[ip] > 0) {
+        LaneSolve<D, T> d;
+        lane_init<D, T, S>(d, pv, ip, kc, ms);
+#pragma unroll
+        for (int c = 0; c < 3; c++) d.vb[c] = (T)pv.vbar[c * pv.cap + ip];
+        deposit_orbit<D, T, FINAL, false>(d.pc, d.cell, d.off, d.dtdx, T(0), T(1), kc.dt, T(1),
+                                          d.vb, nodes, nodes_u, J, pg, kc, ms, win_col, ref,
+                                          npieces, st, work, chain, 2);
+      }
+    }
+    __syncwarp();
+    for (int e = lane; e < WarpWin<D>::NE; e += 32) {
+      const T *rowp = win_warp + (size_t)e * 32;
+      T sum = T(0);
+#pragma unroll 8
+      for (int l = 0; l < 32; l++) sum += rowp[(l + lane) & 31];
+      if (sum != T(0)) {
+        const int node = e / 3, c = e - 3 * node;
+        const int rx = node % WarpWin<D>::N0 + WarpWin<D>::LO0;
+        const int ry = node / WarpWin<D>::N0 + WarpWin<D>::LO1;
+        int g = (ref[0] + rx) & pg.mask[0];
+        if (D > 1) g += pg.n0 * ((ref[1] + ry) & pg.mask[1]);
+        atomicAdd(J + (size_t)c * pg.Ng + g, widen(sum));
+      }
+    }
+  } else {
+    // FP64 and 3D: direct atomics, kPT particles at a time in the order of
+    // s_order (given by the caller, else that of the knot planes the final
+    // orbits cross)
+    __shared__ int s_own[kChunk];
+    if (!s_order) {
+      s_order = s_own;
+      order_chunk<D, T, S>(pv, c0, nvalid, pv.vbar, kc, ms, s_order);
+    }
+#pragma unroll 1
+    for (int q = 0; q < kRefill; q++) {
+      const int kk = q * kPT + threadIdx.x;
+      const int64_t ip = kk < nvalid ? c0 + s_order[kk] : -1;
+      if (ip >= 0 && pv.iters[ip] > 0) {
+        LaneSolve<D, T> d;
+        lane_init<D, T, S>(d, pv, ip, kc, ms);
+#pragma unroll
+        for (int c = 0; c < 3; c++) d.vb[c] = (T)pv.vbar[c * pv.cap + ip];
+        const int ref[3] = {0, 0, 0};
+        deposit_orbit<D, T, FINAL, false>(d.pc, d.cell, d.off, d.dtdx, T(0), T(1), kc.dt, T(1),
+                                          d.vb, nodes, nodes_u, J, pg, kc, ms, nullptr, ref,
+                                          npieces, st, work, chain, 2);
+      }
+    }
+  }
+  if (st) atomicOr(&cnt->status, st);
+  const unsigned pc_w = __reduce_add_sync(0xffffffffu, (unsigned)npieces);
+  if (lane == 0) atomicAdd(&cnt->pieces, (unsigned long long)pc_w);
   if (FINAL) {
     double v[2] = {work, chain};
     block_sums<2>(v, psum);
@@ -1635,12 +1800,60 @@ k_map(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
       double *__restrict__ psum, unsigned long long *__restrict__ tim) {
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
-  if constexpr (!GEN && (std::is_same<T, double>::value || std::is_same<T, float>::value))
-    map_chunk<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, nodes_u, J, pg, kc, ms, cnt,
-                              psum + 2 * (size_t)blockIdx.x);
-  else
-    map_block<D, T, FINAL, GEN, S>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes, nodes_u,
-                                   J, pg, kc, ms, cnt, psum + 2 * (size_t)blockIdx.x);
+  map_block<D, T, FINAL, GEN, S>(pv, blockIdx.x * (int64_t)kPT + threadIdx.x, nodes, nodes_u, J,
+                                 pg, kc, ms, cnt, psum + 2 * (size_t)blockIdx.x);
+  if (tim) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(tim + 1, global_ns());
+  }
+}
+
+// The common path (quadratic shapes, no refinement, FP64 or FP32 arithmetic)
+// as two launches over chunks of kChunk particles: the inner solves with lane
+// refill, then the deposits.  Two kernels rather than one keep each kernel's
+// code small and let the deposit pass start on a chunk without waiting at a
+// barrier for the chunk's slowest inner solve.  tim as for k_map: the solve
+// launch records the start, the deposit launch the end.
+template <int D, typename T, typename S = T>
+__global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 4 : 1)
+k_map_solve(PView<S> pv, const T *__restrict__ nodes, PGeom pg, KConst<T> kc,
+            EvalCounters *__restrict__ cnt, unsigned long long *__restrict__ tim) {
+  if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
+  const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
+  __shared__ int s_order[kChunk];
+  map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order);
+}
+
+template <int D, typename T, bool FINAL, typename S = T>
+__global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 4 : 1)
+k_map_deposit(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
+              double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
+              double *__restrict__ psum, unsigned long long *__restrict__ tim) {
+  const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
+  map_chunk_deposit<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, nodes_u, J, pg, kc,
+                                    ms, cnt, psum + 2 * (size_t)blockIdx.x, nullptr);
+  if (tim) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(tim + 1, global_ns());
+  }
+}
+
+// The same two passes in one launch (FP64 arithmetic): the FP64 map is bound
+// by the FP64 pipe rather than by latency, so the chunk's deposits follow its
+// inner solves in the same CTA, while the particles are still in L2.
+template <int D, typename T, bool FINAL, typename S = T>
+__global__ void __launch_bounds__(kPT, 1)
+k_map_fused(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
+            double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
+            double *__restrict__ psum, unsigned long long *__restrict__ tim) {
+  if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
+  const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
+  __shared__ int s_order[kChunk];
+  map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order);
+  __syncthreads();  // every orbit velocity of the chunk stored
+  // the deposits in the solve's order (predicted crossings)
+  map_chunk_deposit<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, nodes_u, J, pg, kc,
+                                    ms, cnt, psum + 2 * (size_t)blockIdx.x, s_order);
   if (tim) {
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(tim + 1, global_ns());

@@ -5,6 +5,7 @@
 #include "csum.cuh"
 
 #include <cmath>
+#include <type_traits>
 
 namespace {
 
@@ -491,6 +492,38 @@ int particles_step_start(pic_ctx *ctx) {
   return PIC_OK;
 }
 
+// The common path's particle map: the inner-solve launch, then the deposit
+// launch, over chunks of kChunk particles.
+template <int DD, typename RT, bool FIN>
+void map_split_launch(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
+                      unsigned long long *tim) {
+  const KConst<RT> kc = kconst<RT>(sc, pg);
+  if constexpr (std::is_same<RT, double>::value) {  // FP64: one launch (k_map_fused)
+    k_map_fused<DD, RT, FIN><<<nb, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes,
+                                                      (const RT *)ctx->nodes_u, ctx->Jorb, pg, kc,
+                                                      ctx->cnt_dev, ctx->psum, tim);
+    return;
+  }
+  k_map_solve<DD, RT><<<nb, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes, pg, kc,
+                                               ctx->cnt_dev, tim);
+  k_map_deposit<DD, RT, FIN><<<nb, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes,
+                                                      (const RT *)ctx->nodes_u, ctx->Jorb, pg, kc,
+                                                      ctx->cnt_dev, ctx->psum, tim);
+}
+
+// The same for the FP32 stage of an FP64 context: FP32 arithmetic and FP32
+// node records on the FP64 particle storage.
+template <int DD, bool FIN>
+void map_split_launch_f32(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
+                          unsigned long long *tim) {
+  const KConst<float> kc = kconst<float>(sc, pg);
+  k_map_solve<DD, float, double><<<nb, kPT, 0, ctx->st>>>(pview<double>(ctx), ctx->nodes_f, pg,
+                                                          kc, ctx->cnt_dev, tim);
+  k_map_deposit<DD, float, FIN, double><<<nb, kPT, 0, ctx->st>>>(
+      pview<double>(ctx), ctx->nodes_f, ctx->nodes_u_f, ctx->Jorb, pg, kc, ctx->cnt_dev,
+      ctx->psum, tim);
+}
+
 int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
   CK(cudaMemsetAsync(ctx->cnt_dev, 0, sizeof(EvalCounters), ctx->st));
   int nb = nblk(ctx->np);
@@ -513,13 +546,13 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
   PIC_DISPATCH(ctx, (k_map<DD, RT, FIN, GEN><<<nb, kPT, 0, ctx->st>>>(                      \
                          pview<RT>(ctx), (const RT *)ctx->nodes, (const RT *)ctx->nodes_u, \
                          ctx->Jorb, pg, kconst<RT>(sc_in, pg), ctx->cnt_dev, ctx->psum, tim)))
+    // the common path: inner solves, then deposits (two launches)
+#define PIC_MAP_SPLIT(FIN) \
+  PIC_DISPATCH(ctx, (map_split_launch<DD, RT, FIN>(ctx, nb, pg, sc_in, tim)))
     // the general kernels (degree-one shapes, refinement) only when needed
     const bool gen = sc_in.order != 2 || sc_in.refine_max > 0;
     if (ctx->eval_f32) {  // FP32 arithmetic on the FP64 particle storage
-#define PIC_MAP_F32(DD, FIN, GEN)                                                          \
-  k_map<DD, float, FIN, GEN, double><<<nb, kPT, 0, ctx->st>>>(                               \
-      pview<double>(ctx), ctx->nodes_f, ctx->nodes_u_f, ctx->Jorb, pg, kconst<float>(sc_in, pg), \
-      ctx->cnt_dev, ctx->psum, tim)
+#define PIC_MAP_F32(DD, FIN, GEN) map_split_launch_f32<DD, FIN>(ctx, nb, pg, sc_in, tim)
 #define PIC_MAP_F32_D(FIN, GEN)                                                            \
   do {                                                                                     \
     if (ctx->g.dim == 1) PIC_MAP_F32(1, FIN, GEN);                                         \
@@ -537,11 +570,12 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
 #undef PIC_MAP_F32
     } else if (final_pass) {
       if (gen) PIC_MAP_LAUNCH(true, true);
-      else PIC_MAP_LAUNCH(true, false);
+      else PIC_MAP_SPLIT(true);
     } else {
       if (gen) PIC_MAP_LAUNCH(false, true);
-      else PIC_MAP_LAUNCH(false, false);
+      else PIC_MAP_SPLIT(false);
     }
+#undef PIC_MAP_SPLIT
 #undef PIC_MAP_LAUNCH
     KCHECK();
     if (!loop) CK(cudaEventRecordWithFlags(ctx->ev1, ctx->st, evf));
