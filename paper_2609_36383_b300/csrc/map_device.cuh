@@ -1638,6 +1638,28 @@ __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_
   }
 }
 
+// What the deposit of one particle reads: position, orbit velocity, weight
+// and species.
+template <typename T>
+struct DepIn {
+  int cell[3];
+  T off[3], vb[3];
+  double w;
+  int sp;
+};
+
+template <int D, typename T, typename S>
+__device__ __forceinline__ void dep_load(DepIn<T> &o, const PView<S> &pv, int64_t i) {
+#pragma unroll
+  for (int l = 0; l < 3; l++) {
+    o.cell[l] = l < D ? pv.cell[l * pv.cap + i] : 0;
+    o.off[l] = l < D ? (T)pv.off[l * pv.cap + i] : T(0);
+    o.vb[l] = (T)pv.vbar[l * pv.cap + i];
+  }
+  o.w = pv.w[i];
+  o.sp = pv.sp[i];
+}
+
 // The orbit deposits of one chunk from the stored orbit velocities (Eq.
 // orbit-current-energy), and on the final pass the particle sides of the
 // work and chain-rule sums (psum[0..2), the CTA's partials).  Lanes take the
@@ -1706,7 +1728,7 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
       const unsigned b = c == 0 ? bal[q][0] : c == 1 ? bal[q][1] : c == 2 ? bal[q][2] : bal[q][3];
       const int s0 =
           c == 0 ? start[q][0] : c == 1 ? start[q][1] : c == 2 ? start[q][2] : start[q][3];
-      s_dord[wid][s0 + __popc(b & lt)] = (short)(q * 32 + lane);
+      s_dord[wid][s0 + __popc(b & lt)] = (short)(c == 3 ? -1 : q * 32 + lane);
     }
     int ref[3] = {0, 0, 0};
     if (r0 < nvalid) {
@@ -1717,19 +1739,33 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
     T *win_col = win_warp + lane;
     for (int e = 0; e < WarpWin<D>::NE; e++) win_col[e * 32] = T(0);
     __syncwarp();
+    // the deposits; each round's particle data is loaded one round ahead
+    // (slot -1: an empty slot or a failed particle)
+    DepIn<T> cur, nxt;
+    int kcur = s_dord[wid][lane];
+    if (kcur >= 0) dep_load<D, T, S>(cur, pv, c0 + r0 + kcur);
+    T dtdx[3];
+#pragma unroll
+    for (int l = 0; l < 3; l++) dtdx[l] = l < D ? kc.dt * ms.inv_dx[l] : T(0);
 #pragma unroll 1
     for (int q = 0; q < kRefill; q++) {
-      const int k = r0 + s_dord[wid][q * 32 + lane];
-      const int64_t ip = c0 + k;
-      if (k < nvalid && pv.iters[ip] > 0) {
-        LaneSolve<D, T> d;
-        lane_init<D, T, S>(d, pv, ip, kc, ms);
-#pragma unroll
-        for (int c = 0; c < 3; c++) d.vb[c] = (T)pv.vbar[c * pv.cap + ip];
-        deposit_orbit<D, T, FINAL, false>(d.pc, d.cell, d.off, d.dtdx, T(0), T(1), kc.dt, T(1),
-                                          d.vb, nodes, nodes_u, J, pg, kc, ms, win_col, ref,
+      const int knx = q + 1 < kRefill ? s_dord[wid][(q + 1) * 32 + lane] : -1;
+      if (knx >= 0) dep_load<D, T, S>(nxt, pv, c0 + r0 + knx);
+      if (kcur >= 0) {
+        PushConst<T> pc;
+        if (FINAL) {  // the work and chain-rule sums need the push constants
+          LaneSolve<D, T> d;
+          lane_init<D, T, S>(d, pv, c0 + r0 + kcur, kc, ms);
+          pc = d.pc;
+        } else {
+          pc.q = (T)cur.w * kc.qT[cur.sp];
+        }
+        deposit_orbit<D, T, FINAL, false>(pc, cur.cell, cur.off, dtdx, T(0), T(1), kc.dt, T(1),
+                                          cur.vb, nodes, nodes_u, J, pg, kc, ms, win_col, ref,
                                           npieces, st, work, chain, 2);
       }
+      cur = nxt;
+      kcur = knx;
     }
     __syncwarp();
     for (int e = lane; e < WarpWin<D>::NE; e += 32) {
