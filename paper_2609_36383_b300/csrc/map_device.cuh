@@ -1410,6 +1410,13 @@ __device__ __forceinline__ void map_block(const PView<S> &pv, const int64_t i_sl
   }
 }
 
+// the global nanosecond timer
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // ---- the particle map with lane refill -----------------------------------
 //
 // A warp executes each inner sweep for as long as its slowest lane still
@@ -1437,21 +1444,78 @@ struct LaneSolve {
   int it;
 };
 
-template <int D, typename T, typename S>
-__device__ __forceinline__ void lane_init(LaneSolve<D, T> &ls, const PView<S> &pv, int64_t i,
-                                          const KConst<T> &kc, const MapScale<T> &ms) {
-  const int64_t cap = pv.cap;
-  const int s_id = pv.sp[i];
+// Where a particle's step inputs are read: the particle arrays in global
+// memory (GSrc, index = particle slot), or one chunk of them staged in
+// shared memory (StSrc, index = position in the chunk).  vel is v^0, or the
+// last orbit velocity when the inner iteration is warm-started.
+template <typename S>
+struct GSrc {
+  const PView<S> *pv;
+  const S *vel;
+  __device__ __forceinline__ int cell(int l, int64_t i) const { return pv->cell[l * pv->cap + i]; }
+  __device__ __forceinline__ S off(int l, int64_t i) const { return pv->off[l * pv->cap + i]; }
+  __device__ __forceinline__ S P(int c, int64_t i) const { return pv->P[c * pv->cap + i]; }
+  __device__ __forceinline__ S Am(int c, int64_t i) const { return pv->Am[c * pv->cap + i]; }
+  __device__ __forceinline__ S v(int c, int64_t i) const { return vel[c * pv->cap + i]; }
+  __device__ __forceinline__ double w(int64_t i) const { return pv->w[i]; }
+  __device__ __forceinline__ int sp(int64_t i) const { return pv->sp[i]; }
+};
+
+// One chunk of particle inputs in shared memory, one array per component of
+// kChunk entries: cell (D), offset (D), P (3), A^- (3), start velocity (3),
+// weight, species.  Every array starts on a 16-byte boundary (kChunk * 4 is).
+template <int D, typename S>
+struct Stage {
+  static constexpr int kCell = 0;
+  static constexpr int kOff = kCell + D * kChunk * 4;
+  static constexpr int kP = kOff + D * kChunk * (int)sizeof(S);
+  static constexpr int kAm = kP + 3 * kChunk * (int)sizeof(S);
+  static constexpr int kV = kAm + 3 * kChunk * (int)sizeof(S);
+  static constexpr int kW = kV + 3 * kChunk * (int)sizeof(S);
+  static constexpr int kSp = kW + kChunk * 8;
+  static constexpr int kBytes = kSp + kChunk * 4;
+};
+
+template <int D, typename S>
+struct StSrc {
+  const char *base;
+  __device__ __forceinline__ int cell(int l, int64_t k) const {
+    return reinterpret_cast<const int *>(base + Stage<D, S>::kCell)[l * kChunk + k];
+  }
+  __device__ __forceinline__ S off(int l, int64_t k) const {
+    return reinterpret_cast<const S *>(base + Stage<D, S>::kOff)[l * kChunk + k];
+  }
+  __device__ __forceinline__ S P(int c, int64_t k) const {
+    return reinterpret_cast<const S *>(base + Stage<D, S>::kP)[c * kChunk + k];
+  }
+  __device__ __forceinline__ S Am(int c, int64_t k) const {
+    return reinterpret_cast<const S *>(base + Stage<D, S>::kAm)[c * kChunk + k];
+  }
+  __device__ __forceinline__ S v(int c, int64_t k) const {
+    return reinterpret_cast<const S *>(base + Stage<D, S>::kV)[c * kChunk + k];
+  }
+  __device__ __forceinline__ double w(int64_t k) const {
+    return reinterpret_cast<const double *>(base + Stage<D, S>::kW)[k];
+  }
+  __device__ __forceinline__ int sp(int64_t k) const {
+    return reinterpret_cast<const int *>(base + Stage<D, S>::kSp)[k];
+  }
+};
+
+template <int D, typename T, typename Src>
+__device__ __forceinline__ void lane_init_from(LaneSolve<D, T> &ls, const Src &src, int64_t i,
+                                               const KConst<T> &kc, const MapScale<T> &ms) {
+  const int s_id = src.sp(i);
   PushConst<T> &pc = ls.pc;
   if constexpr (std::is_same<T, float>::value) {
     // FP32: the weight rounded once, then FP32 products (no FP64 arithmetic,
     // whose pipe is 1/64 of the FP32 one)
-    const float wf = (float)pv.w[i];
+    const float wf = (float)src.w(i);
     pc.q = wf * kc.qT[s_id];
     pc.m = wf * kc.mT[s_id];
   } else {
-    pc.q = (T)(pv.w[i] * kc.qs[s_id]);
-    pc.m = (T)(pv.w[i] * kc.ms[s_id]);
+    pc.q = (T)(src.w(i) * kc.qs[s_id]);
+    pc.m = (T)(src.w(i) * kc.ms[s_id]);
   }
   const T kap = kc.kappa, dt = kc.dt;
   pc.inv_m = T(1) / pc.m;
@@ -1461,21 +1525,28 @@ __device__ __forceinline__ void lane_init(LaneSolve<D, T> &ls, const PView<S> &p
   pc.a_hc = pc.hq * pc.inv_m;
 #pragma unroll
   for (int l = 0; l < 3; l++) {
-    ls.cell[l] = l < D ? pv.cell[l * cap + i] : 0;
-    ls.off[l] = l < D ? (T)pv.off[l * cap + i] : T(0);
+    ls.cell[l] = l < D ? src.cell(l, i) : 0;
+    ls.off[l] = l < D ? (T)src.off(l, i) : T(0);
     ls.dtdx[l] = l < D ? dt * ms.inv_dx[l] : T(0);
   }
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    pc.Pn[c] = (T)pv.P[c * cap + i];
-    pc.Am[c] = (T)pv.Am[c * cap + i];
+    pc.Pn[c] = (T)src.P(c, i);
+    pc.Am[c] = (T)src.Am(c, i);
     pc.pn[c] = pc.Pn[c] - pc.q * pc.Am[c];
-    ls.vb[c] = (T)(kc.warm ? pv.vbar[c * cap + i] : pv.v0[c * cap + i]);
+    ls.vb[c] = (T)src.v(c, i);
     ls.Pn1[c] = pc.Pn[c];
   }
   pc.gamma_n = sqrt(T(1) + (pc.pn[0] * pc.pn[0] + pc.pn[1] * pc.pn[1] + pc.pn[2] * pc.pn[2]) *
                                pc.inv_mk * pc.inv_mk);
   ls.it = 0;
+}
+
+template <int D, typename T, typename S>
+__device__ __forceinline__ void lane_init(LaneSolve<D, T> &ls, const PView<S> &pv, int64_t i,
+                                          const KConst<T> &kc, const MapScale<T> &ms) {
+  const GSrc<S> src{&pv, kc.warm ? pv.vbar : pv.v0};
+  lane_init_from<D, T>(ls, src, i, kc, ms);
 }
 
 // One inner sweep of the particle a lane holds (the body of picard's loop):
@@ -1524,13 +1595,13 @@ __device__ __forceinline__ int lane_sweep(LaneSolve<D, T> &ls, const T *__restri
   return 0;
 }
 
-// Orders the nvalid particles of the chunk at c0 by the number of knot
-// planes (0, 1, 2 or more) that a straight orbit with velocity vel crosses
-// (stable, deterministic), into s_order.  Ends with a barrier.
-template <int D, typename T, typename S>
-__device__ __forceinline__ void order_chunk(const PView<S> &pv, const int64_t c0, int nvalid,
-                                            const S *__restrict__ vel, const KConst<T> &kc,
-                                            const MapScale<T> &ms, int *s_order) {
+// Orders the nvalid particles of the chunk at c0 (in src's indexing) by the
+// number of knot planes (0, 1, 2 or more) that a straight orbit with velocity
+// src.v crosses (stable, deterministic), into s_order.  Ends with a barrier.
+template <int D, typename T, typename Src>
+__device__ __forceinline__ void order_chunk(const Src &src, const int64_t c0, int nvalid,
+                                            const KConst<T> &kc, const MapScale<T> &ms,
+                                            int *s_order) {
   __shared__ int s_wcnt[kRefill][kPT / 32][4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int cls_of[kRefill];
@@ -1544,7 +1615,7 @@ __device__ __forceinline__ void order_chunk(const PView<S> &pv, const int64_t c0
       cls = 0;
 #pragma unroll
       for (int l = 0; l < D; l++) {
-        const T u = (T)pv.off[l * pv.cap + i] + (T)vel[l * pv.cap + i] * kc.dt * ms.inv_dx[l];
+        const T u = (T)src.off(l, i) + (T)src.v(l, i) * kc.dt * ms.inv_dx[l];
         cls += (u >= T(0.5) || u < T(-0.5)) ? 1 : 0;
       }
       cls = cls < 2 ? cls : 2;
@@ -1574,22 +1645,118 @@ __device__ __forceinline__ void order_chunk(const PView<S> &pv, const int64_t c0
   __syncthreads();
 }
 
+// Bulk asynchronous copies (cp.async.bulk) from global into shared memory,
+// completed on an mbarrier, and a wait on it with a time limit.
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned phase) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+// true when the phase completed; false after limit_ns (or 2^24 polls)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phase,
+                                          unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0; it < (1u << 24); it++) {
+    if (mbar_try_wait(bar, phase)) return true;
+    if ((it & 31u) == 31u && global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+constexpr unsigned long long kStageWaitNs = 200000000ull;  // 0.2 s: copies take microseconds
+
+// Stages the chunk's particle inputs at c0 (kChunk slots of every array;
+// the capacity is a whole number of chunks) into st by one thread's bulk
+// copies; every thread then waits.  False (and PIC_ST_WAIT set) if the copies
+// did not complete in time.
+template <int D, typename S>
+__device__ __forceinline__ bool stage_chunk(const PView<S> &pv, const S *__restrict__ vel,
+                                            int64_t c0, char *st, unsigned long long *bar,
+                                            EvalCounters *__restrict__ cnt) {
+  using L = Stage<D, S>;
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, (unsigned)L::kBytes);
+    const int64_t cap = pv.cap;
+    constexpr unsigned bs = kChunk * sizeof(S), b4 = kChunk * 4;
+#pragma unroll
+    for (int l = 0; l < D; l++) {
+      bulk_g2s(st + L::kCell + l * b4, pv.cell + l * cap + c0, b4, bar);
+      bulk_g2s(st + L::kOff + l * bs, pv.off + l * cap + c0, bs, bar);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      bulk_g2s(st + L::kP + c * bs, pv.P + c * cap + c0, bs, bar);
+      bulk_g2s(st + L::kAm + c * bs, pv.Am + c * cap + c0, bs, bar);
+      bulk_g2s(st + L::kV + c * bs, vel + c * cap + c0, bs, bar);
+    }
+    bulk_g2s(st + L::kW, pv.w + c0, kChunk * 8, bar);
+    bulk_g2s(st + L::kSp, pv.sp + c0, b4, bar);
+  }
+  const bool ok = mbar_wait(bar, 0, kStageWaitNs);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicOr(&cnt->status, PIC_ST_WAIT);
+    mbar_wait(bar, 0, kStageWaitNs);  // let copies in flight land before the CTA exits
+    return false;
+  }
+  return true;
+}
+
 // The inner solves of the particle map over one chunk of kChunk particle
 // slots starting at c0 (the common path: quadratic shapes, no refinement):
 // every particle's orbit velocity, P^{n+1} and inner count (-1 on failure)
-// are stored for the deposit pass (map_chunk_deposit).
+// are stored for the deposit pass (map_chunk_deposit).  With a stage buffer
+// (stg, bar non-null: FP32 arithmetic on FP32 storage) the chunk's inputs are
+// first copied to shared memory, and the ordering and every refill read them
+// there.
 template <int D, typename T, typename S>
 __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_t c0,
                                                 const T *__restrict__ nodes, const PGeom &pg,
                                                 const KConst<T> &kc, const MapScale<T> &ms,
-                                                EvalCounters *__restrict__ cnt, int *s_order) {
+                                                EvalCounters *__restrict__ cnt, int *s_order,
+                                                char *stg, unsigned long long *bar) {
   __shared__ int s_next;
   const int lane = threadIdx.x & 31;
   const int64_t nvalid64 = pv.np - c0;
   const int nvalid = nvalid64 < kChunk ? (int)nvalid64 : kChunk;
   if (threadIdx.x == 0) s_next = 0;
-  // 1. order the chunk by predicted crossing class
-  order_chunk<D, T, S>(pv, c0, nvalid, kc.warm ? pv.vbar : pv.v0, kc, ms, s_order);
+  const S *vel = kc.warm ? pv.vbar : pv.v0;
+  if (stg) {
+    if (!stage_chunk<D, S>(pv, vel, c0, stg, bar, cnt)) return;
+    // 1. order the chunk by predicted crossing class
+    order_chunk<D, T>(StSrc<D, S>{stg}, 0, nvalid, kc, ms, s_order);
+  } else {
+    order_chunk<D, T>(GSrc<S>{&pv, vel}, c0, nvalid, kc, ms, s_order);
+  }
   // 2. the inner solves, lanes refilled from the chunk
   int npieces = 0, mx_it = 0;
   unsigned it_sum = 0;
@@ -1597,8 +1764,14 @@ __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_
   LaneSolve<D, T> ls;
   int k = atomicAdd(&s_next, 1);
   bool have = k < nvalid;
-  int64_t i = have ? c0 + s_order[k] : 0;
-  if (have) lane_init<D, T, S>(ls, pv, i, kc, ms);
+  int kk = have ? s_order[k] : 0;
+  int64_t i = c0 + kk;
+  const StSrc<D, S> ssrc{stg};
+  const GSrc<S> gsrc{&pv, vel};
+  if (have) {
+    if (stg) lane_init_from<D, T>(ls, ssrc, kk, kc, ms);
+    else lane_init_from<D, T>(ls, gsrc, i, kc, ms);
+  }
   while (__any_sync(0xffffffffu, have)) {
     if (have) {
       unsigned int sl = 0;
@@ -1620,8 +1793,10 @@ __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_
         k = atomicAdd(&s_next, 1);
         have = k < nvalid;
         if (have) {
-          i = c0 + s_order[k];
-          lane_init<D, T, S>(ls, pv, i, kc, ms);
+          kk = s_order[k];
+          i = c0 + kk;
+          if (stg) lane_init_from<D, T>(ls, ssrc, kk, kc, ms);
+          else lane_init_from<D, T>(ls, gsrc, i, kc, ms);
         }
       }
     }
@@ -1789,7 +1964,8 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
     __shared__ int s_own[kChunk];
     if (!s_order) {
       s_order = s_own;
-      order_chunk<D, T, S>(pv, c0, nvalid, pv.vbar, kc, ms, s_order);
+      const GSrc<S> src{&pv, pv.vbar};
+      order_chunk<D, T>(src, c0, nvalid, kc, ms, s_order);
     }
 #pragma unroll 1
     for (int q = 0; q < kRefill; q++) {
@@ -1816,12 +1992,6 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
   }
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // FP32 instances: at least 4 resident CTAs (<= 128 registers) to hide latency;
 // FP64 instances are bound by the FP64 pipe and keep their registers.
 // S is the particle storage type: T itself, or double under FP32 arithmetic
@@ -1844,6 +2014,12 @@ k_map(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
   }
 }
 
+// The FP32 solve launch stages each chunk's inputs in shared memory (dynamic
+// shared memory of Stage<D, float>::kBytes); FP64 and the FP32 stage of FP64
+// contexts read them from global memory.
+template <typename T, typename S>
+constexpr bool kStaged = std::is_same<T, float>::value && std::is_same<S, float>::value;
+
 // The common path (quadratic shapes, no refinement, FP64 or FP32 arithmetic)
 // as two launches over chunks of kChunk particles: the inner solves with lane
 // refill, then the deposits.  Two kernels rather than one keep each kernel's
@@ -1857,7 +2033,15 @@ k_map_solve(PView<S> pv, const T *__restrict__ nodes, PGeom pg, KConst<T> kc,
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   __shared__ int s_order[kChunk];
-  map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order);
+  if constexpr (kStaged<T, S>) {
+    extern __shared__ __align__(16) char s_stage[];  // Stage<D, S>::kBytes
+    __shared__ unsigned long long s_bar;
+    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order,
+                             s_stage, &s_bar);
+  } else {
+    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order,
+                             nullptr, nullptr);
+  }
 }
 
 template <int D, typename T, bool FINAL, typename S = T>
@@ -1885,7 +2069,8 @@ k_map_fused(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ node
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   __shared__ int s_order[kChunk];
-  map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order);
+  map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order,
+                           nullptr, nullptr);
   __syncthreads();  // every orbit velocity of the chunk stored
   // the deposits in the solve's order (predicted crossings)
   map_chunk_deposit<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, nodes_u, J, pg, kc,

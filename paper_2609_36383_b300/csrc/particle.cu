@@ -380,7 +380,9 @@ int particles_alloc(pic_ctx *ctx, int64_t n) {
     if (*b) cudaFree(*b);
     *b = nullptr;
   }
-  int64_t cap = n > 0 ? n : 1;
+  // a whole number of map chunks, so that the map's staging copies of a
+  // chunk stay inside every array and start on 16-byte boundaries
+  int64_t cap = ((n > 0 ? n : 1) + kChunk - 1) / kChunk * kChunk;
   size_t R = (size_t)ctx->rsize;
   size_t nb = (size_t)nblk(cap) + 1;
   CK(cudaMalloc((void **)&ctx->cell, sizeof(int32_t) * 3 * cap));
@@ -495,20 +497,26 @@ int particles_step_start(pic_ctx *ctx) {
 // The common path's particle map: the inner-solve launch, then the deposit
 // launch, over chunks of kChunk particles.
 template <int DD, typename RT, bool FIN>
-void map_split_launch(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
-                      unsigned long long *tim) {
+int map_split_launch(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
+                     unsigned long long *tim) {
   const KConst<RT> kc = kconst<RT>(sc, pg);
   if constexpr (std::is_same<RT, double>::value) {  // FP64: one launch (k_map_fused)
     k_map_fused<DD, RT, FIN><<<nb, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes,
                                                       (const RT *)ctx->nodes_u, ctx->Jorb, pg, kc,
                                                       ctx->cnt_dev, ctx->psum, tim);
-    return;
+    return PIC_OK;
   }
-  k_map_solve<DD, RT><<<nb, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes, pg, kc,
-                                               ctx->cnt_dev, tim);
+  // FP32: the chunk's inputs staged in dynamic shared memory
+  const int dsm = kStaged<RT, RT> ? Stage<DD, RT>::kBytes : 0;
+  if (dsm)
+    CK(cudaFuncSetAttribute(k_map_solve<DD, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            dsm));
+  k_map_solve<DD, RT><<<nb, kPT, dsm, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes, pg, kc,
+                                                 ctx->cnt_dev, tim);
   k_map_deposit<DD, RT, FIN><<<nb, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes,
                                                       (const RT *)ctx->nodes_u, ctx->Jorb, pg, kc,
                                                       ctx->cnt_dev, ctx->psum, tim);
+  return PIC_OK;
 }
 
 // The same for the FP32 stage of an FP64 context: FP32 arithmetic and FP32
@@ -547,8 +555,9 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
                          pview<RT>(ctx), (const RT *)ctx->nodes, (const RT *)ctx->nodes_u, \
                          ctx->Jorb, pg, kconst<RT>(sc_in, pg), ctx->cnt_dev, ctx->psum, tim)))
     // the common path: inner solves, then deposits (two launches)
+    int e_split = PIC_OK;
 #define PIC_MAP_SPLIT(FIN) \
-  PIC_DISPATCH(ctx, (map_split_launch<DD, RT, FIN>(ctx, nb, pg, sc_in, tim)))
+  PIC_DISPATCH(ctx, (e_split = map_split_launch<DD, RT, FIN>(ctx, nb, pg, sc_in, tim)))
     // the general kernels (degree-one shapes, refinement) only when needed
     const bool gen = sc_in.order != 2 || sc_in.refine_max > 0;
     if (ctx->eval_f32) {  // FP32 arithmetic on the FP64 particle storage
@@ -577,6 +586,7 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
     }
 #undef PIC_MAP_SPLIT
 #undef PIC_MAP_LAUNCH
+    if (e_split) return e_split;
     KCHECK();
     if (!loop) CK(cudaEventRecordWithFlags(ctx->ev1, ctx->st, evf));
     if (ctx->opt.deterministic_deposit) {  // replaces the atomic deposit in Jorb

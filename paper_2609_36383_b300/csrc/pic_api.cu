@@ -263,7 +263,11 @@ int eval_map(pic_ctx *ctx, const double *jdev, double *Hdev, double *rdev, const
   CK(cudaStreamSynchronize(ctx->st));
   if ((e = particles_map_finish(ctx, &ev->work_p, &ev->chain, &ev->cnt))) return e;
   if (ev->cnt.status) {
-    ctx->err = "inner particle solve failed (status bits " + std::to_string(ev->cnt.status) + ")";
+    ctx->err = (ev->cnt.status & PIC_ST_WAIT)
+                   ? "a bounded device wait gave up (status bits " +
+                         std::to_string(ev->cnt.status) + ")"
+                   : "inner particle solve failed (status bits " + std::to_string(ev->cnt.status) +
+                         ")";
     return PIC_EINNER;
   }
   ResidSums s;

@@ -18,6 +18,7 @@
 #define PIC_ST_NONFINITE 2u   // non-finite orbit velocity
 #define PIC_ST_SUPERLUM 4u    // |vbar| >= kappa
 #define PIC_ST_PIECES 8u      // orbit crosses more knots than the kernel handles
+#define PIC_ST_WAIT 16u       // a bounded device wait (staging copies) gave up
 
 // reals per gather record: [grad phi^{1/2} (d), A^n (3), A^{n+1} (3)] padded
 // to a multiple of four so that records load with 16-byte vector loads
