@@ -1422,7 +1422,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // A warp executes each inner sweep for as long as its slowest lane still
 // iterates, so in map_block the lanes whose particles converged early idle
 // until the warp's last particle converges.  map_chunk_solve removes that
-// wait: a CTA owns a chunk of kRefill * kPT particles, and a lane whose
+// wait: a CTA owns a chunk of kRefillOf<T> * kPT particles, and a lane whose
 // particle has converged (or failed) stores it and takes the next particle of
 // the chunk from a shared counter, so the sweeps run with full warps until
 // the chunk runs dry.  The chunk is ordered by the predicted number of knot
@@ -1432,8 +1432,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // arithmetic (k_map_solve, k_map_deposit), in the same CTA after a barrier
 // for FP64 (k_map_fused).  Every particle's arithmetic is that of map_block:
 // only which lane computes it, and when, changes.
-constexpr int kRefill = 4;
-constexpr int kChunk = kRefill * kPT;
+// Chunk of particles per CTA: 8 x kPT for FP64 arithmetic (longer chunks
+// shorten the share of the drain at each chunk's end), 4 x kPT for FP32
+// (whose inputs are staged in shared memory, chunk by chunk).
+template <typename T>
+constexpr int kRefillOf = sizeof(T) == 8 ? 8 : 4;
+template <typename T>
+constexpr int kChunkOf = kRefillOf<T> * kPT;
+constexpr int kChunk = kChunkOf<float>;        // the FP32 staging chunk
+constexpr int kChunkMax = kChunkOf<double>;    // the longest chunk
 
 // one particle's inner solve between sweeps
 template <int D, typename T>
@@ -1602,12 +1609,12 @@ template <int D, typename T, typename Src>
 __device__ __forceinline__ void order_chunk(const Src &src, const int64_t c0, int nvalid,
                                             const KConst<T> &kc, const MapScale<T> &ms,
                                             int *s_order) {
-  __shared__ int s_wcnt[kRefill][kPT / 32][4];
+  __shared__ int s_wcnt[kRefillOf<T>][kPT / 32][4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int cls_of[kRefill];
-  unsigned mine[kRefill];
+  int cls_of[kRefillOf<T>];
+  unsigned mine[kRefillOf<T>];
 #pragma unroll
-  for (int q = 0; q < kRefill; q++) {
+  for (int q = 0; q < kRefillOf<T>; q++) {
     const int k = q * kPT + threadIdx.x;
     int cls = 3;
     if (k < nvalid) {
@@ -1631,11 +1638,11 @@ __device__ __forceinline__ void order_chunk(const Src &src, const int64_t c0, in
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < kRefill; q++) {
+  for (int q = 0; q < kRefillOf<T>; q++) {
     const int cls = cls_of[q];
     int pos = __popc(mine[q] & ((1u << lane) - 1u));
     for (int c = 0; c < cls; c++)
-      for (int qq = 0; qq < kRefill; qq++)
+      for (int qq = 0; qq < kRefillOf<T>; qq++)
         for (int w = 0; w < kPT / 32; w++) pos += s_wcnt[qq][w][c];
     for (int qq = 0; qq < q; qq++)
       for (int w = 0; w < kPT / 32; w++) pos += s_wcnt[qq][w][cls];
@@ -1731,7 +1738,7 @@ __device__ __forceinline__ bool stage_chunk(const PView<S> &pv, const S *__restr
   return true;
 }
 
-// The inner solves of the particle map over one chunk of kChunk particle
+// The inner solves of the particle map over one chunk of kChunkOf<T> particle
 // slots starting at c0 (the common path: quadratic shapes, no refinement):
 // every particle's orbit velocity, P^{n+1} and inner count (-1 on failure)
 // are stored for the deposit pass (map_chunk_deposit).  With a stage buffer
@@ -1747,7 +1754,7 @@ __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_
   __shared__ int s_next;
   const int lane = threadIdx.x & 31;
   const int64_t nvalid64 = pv.np - c0;
-  const int nvalid = nvalid64 < kChunk ? (int)nvalid64 : kChunk;
+  const int nvalid = nvalid64 < kChunkOf<T> ? (int)nvalid64 : kChunkOf<T>;
   if (threadIdx.x == 0) s_next = 0;
   const S *vel = kc.warm ? pv.vbar : pv.v0;
   if (stg) {
@@ -1837,13 +1844,13 @@ __device__ __forceinline__ void dep_load(DepIn<T> &o, const PView<S> &pv, int64_
 
 // The orbit deposits of one chunk from the stored orbit velocities (Eq.
 // orbit-current-energy), and on the final pass the particle sides of the
-// work and chain-rule sums (psum[0..2), the CTA's partials).  Lanes take the
+// work and chain-rule sums (added to the thread's work and chain).  Lanes take the
 // particles in order of the knot planes their orbits cross, so that a warp's
 // lanes walk similar numbers of pieces.  FP32 in 1D and 2D: warp w deposits
-// the chunk slots [w R, (w + 1) R), R = kRefill * 32, ordered within that
+// the chunk slots [w R, (w + 1) R), R = kRefillOf<T> * 32, ordered within that
 // range; the particles are sorted by cell, so the range lies in one or two
 // neighbouring cells, and one warp window, referenced to the range's first
-// cell, collects all kRefill rounds (cleared and summed once per chunk).
+// cell, collects all kRefillOf<T> rounds (cleared and summed once per chunk).
 // FP64 and 3D: the whole chunk is ordered and deposited with global atomics.
 template <int D, typename T, bool FINAL, typename S>
 __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int64_t c0,
@@ -1852,23 +1859,21 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
                                                   double *__restrict__ J, const PGeom &pg,
                                                   const KConst<T> &kc, const MapScale<T> &ms,
                                                   EvalCounters *__restrict__ cnt,
-                                                  double *__restrict__ psum,
-                                                  int *s_order) {
-  constexpr int R = kRefill * 32;
+                                                  double &work, double &chain, int *s_order) {
+  constexpr int R = kRefillOf<T> * 32;
   constexpr bool kWin = WarpWin<D>::kOn && sizeof(T) == 4;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nvalid64 = pv.np - c0;
-  const int nvalid = nvalid64 < kChunk ? (int)nvalid64 : kChunk;
+  const int nvalid = nvalid64 < kChunkOf<T> ? (int)nvalid64 : kChunkOf<T>;
   int npieces = 0;
   unsigned int st = 0;
-  double work = 0.0, chain = 0.0;
   if constexpr (kWin) {
     __shared__ T s_win[(kPT / 32) * WarpWin<D>::NE * 32];
     __shared__ short s_dord[kPT / 32][R];
     const int r0 = wid * R;
-    int cls_q[kRefill];
+    int cls_q[kRefillOf<T>];
 #pragma unroll
-    for (int q = 0; q < kRefill; q++) {
+    for (int q = 0; q < kRefillOf<T>; q++) {
       const int k = r0 + q * 32 + lane;
       int cls = 3;  // empty slot or failed particle: last
       if (k < nvalid && pv.iters[c0 + k] > 0) {
@@ -1885,20 +1890,20 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
     }
     // stable order by class (class, then round, then lane): the start of
     // round q's slots of class c is warp-uniform, from the ballots' counts
-    unsigned bal[kRefill][4];
-    int start[kRefill][4];
+    unsigned bal[kRefillOf<T>][4];
+    int start[kRefillOf<T>][4];
     int acc = 0;
 #pragma unroll
     for (int c = 0; c < 4; c++)
 #pragma unroll
-      for (int q = 0; q < kRefill; q++) {
+      for (int q = 0; q < kRefillOf<T>; q++) {
         bal[q][c] = __ballot_sync(0xffffffffu, cls_q[q] == c);
         start[q][c] = acc;
         acc += __popc(bal[q][c]);
       }
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int q = 0; q < kRefill; q++) {
+    for (int q = 0; q < kRefillOf<T>; q++) {
       const int c = cls_q[q];
       const unsigned b = c == 0 ? bal[q][0] : c == 1 ? bal[q][1] : c == 2 ? bal[q][2] : bal[q][3];
       const int s0 =
@@ -1923,8 +1928,8 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
 #pragma unroll
     for (int l = 0; l < 3; l++) dtdx[l] = l < D ? kc.dt * ms.inv_dx[l] : T(0);
 #pragma unroll 1
-    for (int q = 0; q < kRefill; q++) {
-      const int knx = q + 1 < kRefill ? s_dord[wid][(q + 1) * 32 + lane] : -1;
+    for (int q = 0; q < kRefillOf<T>; q++) {
+      const int knx = q + 1 < kRefillOf<T> ? s_dord[wid][(q + 1) * 32 + lane] : -1;
       if (knx >= 0) dep_load<D, T, S>(nxt, pv, c0 + r0 + knx);
       if (kcur >= 0) {
         PushConst<T> pc;
@@ -1961,14 +1966,14 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
     // FP64 and 3D: direct atomics, kPT particles at a time in the order of
     // s_order (given by the caller, else that of the knot planes the final
     // orbits cross)
-    __shared__ int s_own[kChunk];
+    __shared__ int s_own[kChunkOf<T>];
     if (!s_order) {
       s_order = s_own;
       const GSrc<S> src{&pv, pv.vbar};
       order_chunk<D, T>(src, c0, nvalid, kc, ms, s_order);
     }
 #pragma unroll 1
-    for (int q = 0; q < kRefill; q++) {
+    for (int q = 0; q < kRefillOf<T>; q++) {
       const int kk = q * kPT + threadIdx.x;
       const int64_t ip = kk < nvalid ? c0 + s_order[kk] : -1;
       if (ip >= 0 && pv.iters[ip] > 0) {
@@ -1986,10 +1991,6 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
   if (st) atomicOr(&cnt->status, st);
   const unsigned pc_w = __reduce_add_sync(0xffffffffu, (unsigned)npieces);
   if (lane == 0) atomicAdd(&cnt->pieces, (unsigned long long)pc_w);
-  if (FINAL) {
-    double v[2] = {work, chain};
-    block_sums<2>(v, psum);
-  }
 }
 
 // FP32 instances: at least 4 resident CTAs (<= 128 registers) to hide latency;
@@ -2021,7 +2022,7 @@ template <typename T, typename S>
 constexpr bool kStaged = std::is_same<T, float>::value && std::is_same<S, float>::value;
 
 // The common path (quadratic shapes, no refinement, FP64 or FP32 arithmetic)
-// as two launches over chunks of kChunk particles: the inner solves with lane
+// as two launches over chunks of kChunkOf<T> particles: the inner solves with lane
 // refill, then the deposits.  Two kernels rather than one keep each kernel's
 // code small and let the deposit pass start on a chunk without waiting at a
 // barrier for the chunk's slowest inner solve.  tim as for k_map: the solve
@@ -2032,14 +2033,14 @@ k_map_solve(PView<S> pv, const T *__restrict__ nodes, PGeom pg, KConst<T> kc,
             EvalCounters *__restrict__ cnt, unsigned long long *__restrict__ tim) {
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
-  __shared__ int s_order[kChunk];
+  __shared__ int s_order[kChunkOf<T>];
   if constexpr (kStaged<T, S>) {
     extern __shared__ __align__(16) char s_stage[];  // Stage<D, S>::kBytes
     __shared__ unsigned long long s_bar;
-    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order,
+    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunkOf<T>, nodes, pg, kc, ms, cnt, s_order,
                              s_stage, &s_bar);
   } else {
-    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order,
+    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunkOf<T>, nodes, pg, kc, ms, cnt, s_order,
                              nullptr, nullptr);
   }
 }
@@ -2050,8 +2051,13 @@ k_map_deposit(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ no
               double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
               double *__restrict__ psum, unsigned long long *__restrict__ tim) {
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
-  map_chunk_deposit<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, nodes_u, J, pg, kc,
-                                    ms, cnt, psum + 2 * (size_t)blockIdx.x, nullptr);
+  double work = 0.0, chain = 0.0;
+  map_chunk_deposit<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunkOf<T>, nodes, nodes_u, J, pg,
+                                    kc, ms, cnt, work, chain, nullptr);
+  if (FINAL) {
+    double v[2] = {work, chain};
+    block_sums<2>(v, psum + 2 * (size_t)blockIdx.x);
+  }
   if (tim) {
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(tim + 1, global_ns());
@@ -2059,22 +2065,39 @@ k_map_deposit(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ no
 }
 
 // The same two passes in one launch (FP64 arithmetic): the FP64 map is bound
-// by the FP64 pipe rather than by latency, so the chunk's deposits follow its
-// inner solves in the same CTA, while the particles are still in L2.
+// by the FP64 pipe rather than by latency, so a chunk's deposits follow its
+// inner solves in the same CTA, while the particles are still in L2.  The
+// grid is persistent (as many CTAs as fit at once): each CTA takes chunks
+// from a counter until nchunks are done, so no partial last wave of CTAs
+// idles the SMs.  psum[2 c .. 2 c + 2) receives chunk c's final-pass partials.
 template <int D, typename T, bool FINAL, typename S = T>
 __global__ void __launch_bounds__(kPT, 1)
 k_map_fused(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
             double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
-            double *__restrict__ psum, unsigned long long *__restrict__ tim) {
+            double *__restrict__ psum, unsigned long long *__restrict__ tim, int nchunks) {
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
-  __shared__ int s_order[kChunk];
-  map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, pg, kc, ms, cnt, s_order,
-                           nullptr, nullptr);
-  __syncthreads();  // every orbit velocity of the chunk stored
-  // the deposits in the solve's order (predicted crossings)
-  map_chunk_deposit<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunk, nodes, nodes_u, J, pg, kc,
-                                    ms, cnt, psum + 2 * (size_t)blockIdx.x, s_order);
+  __shared__ int s_order[kChunkOf<T>];
+  __shared__ int s_chunk;
+#pragma unroll 1
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = (int)atomicAdd(&cnt->chunk_next, 1u);
+    __syncthreads();
+    const int ch = s_chunk;
+    if (ch >= nchunks) break;
+    const int64_t c0 = ch * (int64_t)kChunkOf<T>;
+    map_chunk_solve<D, T, S>(pv, c0, nodes, pg, kc, ms, cnt, s_order, nullptr, nullptr);
+    __syncthreads();  // every orbit velocity of the chunk stored
+    // the deposits in the solve's order (predicted crossings)
+    double work = 0.0, chain = 0.0;
+    map_chunk_deposit<D, T, FINAL, S>(pv, c0, nodes, nodes_u, J, pg, kc, ms, cnt, work, chain,
+                                      s_order);
+    if (FINAL) {  // per-chunk partials: merged in chunk order, whichever CTA ran the chunk
+      double v[2] = {work, chain};
+      block_sums<2>(v, psum + 2 * (size_t)ch);
+    }
+    __syncthreads();  // s_order and s_chunk are reused by the next chunk
+  }
   if (tim) {
     __syncthreads();
     if (threadIdx.x == 0) atomicMax(tim + 1, global_ns());

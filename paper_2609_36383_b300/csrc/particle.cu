@@ -382,7 +382,7 @@ int particles_alloc(pic_ctx *ctx, int64_t n) {
   }
   // a whole number of map chunks, so that the map's staging copies of a
   // chunk stay inside every array and start on 16-byte boundaries
-  int64_t cap = ((n > 0 ? n : 1) + kChunk - 1) / kChunk * kChunk;
+  int64_t cap = ((n > 0 ? n : 1) + kChunkMax - 1) / kChunkMax * kChunkMax;
   size_t R = (size_t)ctx->rsize;
   size_t nb = (size_t)nblk(cap) + 1;
   CK(cudaMalloc((void **)&ctx->cell, sizeof(int32_t) * 3 * cap));
@@ -495,15 +495,20 @@ int particles_step_start(pic_ctx *ctx) {
 }
 
 // The common path's particle map: the inner-solve launch, then the deposit
-// launch, over chunks of kChunk particles.
+// launch, over chunks of kChunkOf<RT> particles.
 template <int DD, typename RT, bool FIN>
 int map_split_launch(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
                      unsigned long long *tim) {
   const KConst<RT> kc = kconst<RT>(sc, pg);
-  if constexpr (std::is_same<RT, double>::value) {  // FP64: one launch (k_map_fused)
-    k_map_fused<DD, RT, FIN><<<nb, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes,
-                                                      (const RT *)ctx->nodes_u, ctx->Jorb, pg, kc,
-                                                      ctx->cnt_dev, ctx->psum, tim);
+  if constexpr (std::is_same<RT, double>::value) {
+    // FP64: one persistent launch (k_map_fused), as many CTAs as fit at once
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_map_fused<DD, RT, FIN>, kPT, 0));
+    int grid = (per_sm > 0 ? per_sm : 1) * ctx->num_sms;
+    grid = grid < nb ? grid : nb;
+    k_map_fused<DD, RT, FIN><<<grid, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes,
+                                                        (const RT *)ctx->nodes_u, ctx->Jorb, pg,
+                                                        kc, ctx->cnt_dev, ctx->psum, tim, nb);
     return PIC_OK;
   }
   // FP32: the chunk's inputs staged in dynamic shared memory
@@ -547,9 +552,12 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
     const unsigned evf = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (!loop) CK(cudaEventRecordWithFlags(ctx->ev0, ctx->st, evf));
     unsigned long long *tim = loop ? ctx->map_timer : nullptr;
-    // the common path runs the lane-refill map over chunks of kChunk
+    // the common path runs the lane-refill map over chunks of kChunkOf<RT>
     // particles; the general path one particle per thread
-    if (!(sc_in.order != 2 || sc_in.refine_max > 0)) nb = (int)((ctx->np + kChunk - 1) / kChunk);
+    if (!(sc_in.order != 2 || sc_in.refine_max > 0)) {
+      const int chunk = ctx->rsize == 8 && !ctx->eval_f32 ? kChunkOf<double> : kChunkOf<float>;
+      nb = (int)((ctx->np + chunk - 1) / chunk);
+    }
 #define PIC_MAP_LAUNCH(FIN, GEN)                                                          \
   PIC_DISPATCH(ctx, (k_map<DD, RT, FIN, GEN><<<nb, kPT, 0, ctx->st>>>(                      \
                          pview<RT>(ctx), (const RT *)ctx->nodes, (const RT *)ctx->nodes_u, \

@@ -52,6 +52,7 @@ struct EvalCounters {
   unsigned long long inner_sum;
   unsigned long long pieces;
   unsigned long long refined;  // particles solved with substeps
+  unsigned int chunk_next;     // chunk queue of the persistent FP64 map kernel
 };
 
 // The spectral field state (accepted, candidate, or a tangent of either).
