@@ -1700,33 +1700,35 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned phas
 
 constexpr unsigned long long kStageWaitNs = 200000000ull;  // 0.2 s: copies take microseconds
 
-// Stages the chunk's particle inputs at c0 (kChunk slots of every array;
-// the capacity is a whole number of chunks) into st by one thread's bulk
-// copies; every thread then waits.  False (and PIC_ST_WAIT set) if the copies
-// did not complete in time.
+// Stages the inputs of the chunk of `chunk` particle slots at c0 (a multiple
+// of kPT, at most kChunk; the capacity is a whole number of the longest
+// chunks, so every copy stays inside its array and starts on a 16-byte
+// boundary) into st by one thread's bulk copies; every thread then waits.
+// False (and PIC_ST_WAIT set) if the copies did not complete in time.
 template <int D, typename S>
 __device__ __forceinline__ bool stage_chunk(const PView<S> &pv, const S *__restrict__ vel,
-                                            int64_t c0, char *st, unsigned long long *bar,
+                                            int64_t c0, int chunk, char *st,
+                                            unsigned long long *bar,
                                             EvalCounters *__restrict__ cnt) {
   using L = Stage<D, S>;
   if (threadIdx.x == 0) mbar_init(bar, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, (unsigned)L::kBytes);
+    const unsigned bs = chunk * (unsigned)sizeof(S), b4 = chunk * 4u;
+    mbar_expect_tx(bar, D * b4 + (D + 9) * bs + chunk * 8u + b4);
     const int64_t cap = pv.cap;
-    constexpr unsigned bs = kChunk * sizeof(S), b4 = kChunk * 4;
 #pragma unroll
     for (int l = 0; l < D; l++) {
-      bulk_g2s(st + L::kCell + l * b4, pv.cell + l * cap + c0, b4, bar);
-      bulk_g2s(st + L::kOff + l * bs, pv.off + l * cap + c0, bs, bar);
+      bulk_g2s(st + L::kCell + l * kChunk * 4, pv.cell + l * cap + c0, b4, bar);
+      bulk_g2s(st + L::kOff + l * kChunk * sizeof(S), pv.off + l * cap + c0, bs, bar);
     }
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      bulk_g2s(st + L::kP + c * bs, pv.P + c * cap + c0, bs, bar);
-      bulk_g2s(st + L::kAm + c * bs, pv.Am + c * cap + c0, bs, bar);
-      bulk_g2s(st + L::kV + c * bs, vel + c * cap + c0, bs, bar);
+      bulk_g2s(st + L::kP + c * kChunk * sizeof(S), pv.P + c * cap + c0, bs, bar);
+      bulk_g2s(st + L::kAm + c * kChunk * sizeof(S), pv.Am + c * cap + c0, bs, bar);
+      bulk_g2s(st + L::kV + c * kChunk * sizeof(S), vel + c * cap + c0, bs, bar);
     }
-    bulk_g2s(st + L::kW, pv.w + c0, kChunk * 8, bar);
+    bulk_g2s(st + L::kW, pv.w + c0, chunk * 8u, bar);
     bulk_g2s(st + L::kSp, pv.sp + c0, b4, bar);
   }
   const bool ok = mbar_wait(bar, 0, kStageWaitNs);
@@ -1738,8 +1740,9 @@ __device__ __forceinline__ bool stage_chunk(const PView<S> &pv, const S *__restr
   return true;
 }
 
-// The inner solves of the particle map over one chunk of kChunkOf<T> particle
-// slots starting at c0 (the common path: quadratic shapes, no refinement):
+// The inner solves of the particle map over one chunk of nr * kPT particle
+// slots (nr <= kRefillOf<T>) starting at c0 (the common path: quadratic
+// shapes, no refinement):
 // every particle's orbit velocity, P^{n+1} and inner count (-1 on failure)
 // are stored for the deposit pass (map_chunk_deposit).  With a stage buffer
 // (stg, bar non-null: FP32 arithmetic on FP32 storage) the chunk's inputs are
@@ -1750,15 +1753,16 @@ __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_
                                                 const T *__restrict__ nodes, const PGeom &pg,
                                                 const KConst<T> &kc, const MapScale<T> &ms,
                                                 EvalCounters *__restrict__ cnt, int *s_order,
-                                                char *stg, unsigned long long *bar) {
+                                                char *stg, unsigned long long *bar, int nr) {
   __shared__ int s_next;
   const int lane = threadIdx.x & 31;
+  const int chunk = nr * kPT;
   const int64_t nvalid64 = pv.np - c0;
-  const int nvalid = nvalid64 < kChunkOf<T> ? (int)nvalid64 : kChunkOf<T>;
+  const int nvalid = nvalid64 < chunk ? (int)nvalid64 : chunk;
   if (threadIdx.x == 0) s_next = 0;
   const S *vel = kc.warm ? pv.vbar : pv.v0;
   if (stg) {
-    if (!stage_chunk<D, S>(pv, vel, c0, stg, bar, cnt)) return;
+    if (!stage_chunk<D, S>(pv, vel, c0, chunk, stg, bar, cnt)) return;
     // 1. order the chunk by predicted crossing class
     order_chunk<D, T>(StSrc<D, S>{stg}, 0, nvalid, kc, ms, s_order);
   } else {
@@ -1859,24 +1863,26 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
                                                   double *__restrict__ J, const PGeom &pg,
                                                   const KConst<T> &kc, const MapScale<T> &ms,
                                                   EvalCounters *__restrict__ cnt,
-                                                  double &work, double &chain, int *s_order) {
-  constexpr int R = kRefillOf<T> * 32;
+                                                  double &work, double &chain, int *s_order,
+                                                  int nr) {
+  constexpr int R = kRefillOf<T> * 32;  // the longest warp range
   constexpr bool kWin = WarpWin<D>::kOn && sizeof(T) == 4;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int chunk = nr * kPT;
   const int64_t nvalid64 = pv.np - c0;
-  const int nvalid = nvalid64 < kChunkOf<T> ? (int)nvalid64 : kChunkOf<T>;
+  const int nvalid = nvalid64 < chunk ? (int)nvalid64 : chunk;
   int npieces = 0;
   unsigned int st = 0;
   if constexpr (kWin) {
     __shared__ T s_win[(kPT / 32) * WarpWin<D>::NE * 32];
     __shared__ short s_dord[kPT / 32][R];
-    const int r0 = wid * R;
+    const int r0 = wid * nr * 32;  // this warp's range: nr rounds of 32
     int cls_q[kRefillOf<T>];
 #pragma unroll
     for (int q = 0; q < kRefillOf<T>; q++) {
       const int k = r0 + q * 32 + lane;
-      int cls = 3;  // empty slot or failed particle: last
-      if (k < nvalid && pv.iters[c0 + k] > 0) {
+      int cls = 3;  // empty slot, failed particle, or a round past nr: last
+      if (q < nr && k < nvalid && pv.iters[c0 + k] > 0) {
         const int64_t i = c0 + k;
         cls = 0;
 #pragma unroll
@@ -1928,8 +1934,8 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
 #pragma unroll
     for (int l = 0; l < 3; l++) dtdx[l] = l < D ? kc.dt * ms.inv_dx[l] : T(0);
 #pragma unroll 1
-    for (int q = 0; q < kRefillOf<T>; q++) {
-      const int knx = q + 1 < kRefillOf<T> ? s_dord[wid][(q + 1) * 32 + lane] : -1;
+    for (int q = 0; q < nr; q++) {
+      const int knx = q + 1 < nr ? s_dord[wid][(q + 1) * 32 + lane] : -1;
       if (knx >= 0) dep_load<D, T, S>(nxt, pv, c0 + r0 + knx);
       if (kcur >= 0) {
         PushConst<T> pc;
@@ -1966,14 +1972,14 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
     // FP64 and 3D: direct atomics, kPT particles at a time in the order of
     // s_order (given by the caller, else that of the knot planes the final
     // orbits cross)
-    __shared__ int s_own[kChunkOf<T>];
+    __shared__ int s_own[kChunkOf<T>];  // room for the longest chunk
     if (!s_order) {
       s_order = s_own;
       const GSrc<S> src{&pv, pv.vbar};
       order_chunk<D, T>(src, c0, nvalid, kc, ms, s_order);
     }
 #pragma unroll 1
-    for (int q = 0; q < kRefillOf<T>; q++) {
+    for (int q = 0; q < nr; q++) {
       const int kk = q * kPT + threadIdx.x;
       const int64_t ip = kk < nvalid ? c0 + s_order[kk] : -1;
       if (ip >= 0 && pv.iters[ip] > 0) {
@@ -2022,7 +2028,8 @@ template <typename T, typename S>
 constexpr bool kStaged = std::is_same<T, float>::value && std::is_same<S, float>::value;
 
 // The common path (quadratic shapes, no refinement, FP64 or FP32 arithmetic)
-// as two launches over chunks of kChunkOf<T> particles: the inner solves with lane
+// as two launches over chunks of nr * kPT particles (nr <= kRefillOf<T>,
+// chosen by the host for the problem size): the inner solves with lane
 // refill, then the deposits.  Two kernels rather than one keep each kernel's
 // code small and let the deposit pass start on a chunk without waiting at a
 // barrier for the chunk's slowest inner solve.  tim as for k_map: the solve
@@ -2030,18 +2037,18 @@ constexpr bool kStaged = std::is_same<T, float>::value && std::is_same<S, float>
 template <int D, typename T, typename S = T>
 __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 4 : 1)
 k_map_solve(PView<S> pv, const T *__restrict__ nodes, PGeom pg, KConst<T> kc,
-            EvalCounters *__restrict__ cnt, unsigned long long *__restrict__ tim) {
+            EvalCounters *__restrict__ cnt, unsigned long long *__restrict__ tim, int nr) {
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   __shared__ int s_order[kChunkOf<T>];
   if constexpr (kStaged<T, S>) {
     extern __shared__ __align__(16) char s_stage[];  // Stage<D, S>::kBytes
     __shared__ unsigned long long s_bar;
-    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunkOf<T>, nodes, pg, kc, ms, cnt, s_order,
-                             s_stage, &s_bar);
+    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)(nr * kPT), nodes, pg, kc, ms, cnt,
+                             s_order, s_stage, &s_bar, nr);
   } else {
-    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)kChunkOf<T>, nodes, pg, kc, ms, cnt, s_order,
-                             nullptr, nullptr);
+    map_chunk_solve<D, T, S>(pv, blockIdx.x * (int64_t)(nr * kPT), nodes, pg, kc, ms, cnt,
+                             s_order, nullptr, nullptr, nr);
   }
 }
 
@@ -2049,11 +2056,11 @@ template <int D, typename T, bool FINAL, typename S = T>
 __global__ void __launch_bounds__(kPT, sizeof(T) == 4 ? 4 : 1)
 k_map_deposit(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
               double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
-              double *__restrict__ psum, unsigned long long *__restrict__ tim) {
+              double *__restrict__ psum, unsigned long long *__restrict__ tim, int nr) {
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   double work = 0.0, chain = 0.0;
-  map_chunk_deposit<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)kChunkOf<T>, nodes, nodes_u, J, pg,
-                                    kc, ms, cnt, work, chain, nullptr);
+  map_chunk_deposit<D, T, FINAL, S>(pv, blockIdx.x * (int64_t)(nr * kPT), nodes, nodes_u, J, pg,
+                                    kc, ms, cnt, work, chain, nullptr, nr);
   if (FINAL) {
     double v[2] = {work, chain};
     block_sums<2>(v, psum + 2 * (size_t)blockIdx.x);
@@ -2074,7 +2081,8 @@ template <int D, typename T, bool FINAL, typename S = T>
 __global__ void __launch_bounds__(kPT, 1)
 k_map_fused(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ nodes_u,
             double *__restrict__ J, PGeom pg, KConst<T> kc, EvalCounters *__restrict__ cnt,
-            double *__restrict__ psum, unsigned long long *__restrict__ tim, int nchunks) {
+            double *__restrict__ psum, unsigned long long *__restrict__ tim, int nchunks,
+            int nr) {
   if (tim && threadIdx.x == 0) atomicMin(tim, global_ns());
   const MapScale<T> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   __shared__ int s_order[kChunkOf<T>];
@@ -2085,13 +2093,13 @@ k_map_fused(PView<S> pv, const T *__restrict__ nodes, const T *__restrict__ node
     __syncthreads();
     const int ch = s_chunk;
     if (ch >= nchunks) break;
-    const int64_t c0 = ch * (int64_t)kChunkOf<T>;
-    map_chunk_solve<D, T, S>(pv, c0, nodes, pg, kc, ms, cnt, s_order, nullptr, nullptr);
+    const int64_t c0 = ch * (int64_t)(nr * kPT);
+    map_chunk_solve<D, T, S>(pv, c0, nodes, pg, kc, ms, cnt, s_order, nullptr, nullptr, nr);
     __syncthreads();  // every orbit velocity of the chunk stored
     // the deposits in the solve's order (predicted crossings)
     double work = 0.0, chain = 0.0;
     map_chunk_deposit<D, T, FINAL, S>(pv, c0, nodes, nodes_u, J, pg, kc, ms, cnt, work, chain,
-                                      s_order);
+                                      s_order, nr);
     if (FINAL) {  // per-chunk partials: merged in chunk order, whichever CTA ran the chunk
       double v[2] = {work, chain};
       block_sums<2>(v, psum + 2 * (size_t)ch);

@@ -497,7 +497,7 @@ int particles_step_start(pic_ctx *ctx) {
 // The common path's particle map: the inner-solve launch, then the deposit
 // launch, over chunks of kChunkOf<RT> particles.
 template <int DD, typename RT, bool FIN>
-int map_split_launch(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
+int map_split_launch(pic_ctx *ctx, int nb, int nr, const PGeom &pg, const StepConst &sc,
                      unsigned long long *tim) {
   const KConst<RT> kc = kconst<RT>(sc, pg);
   if constexpr (std::is_same<RT, double>::value) {
@@ -508,7 +508,7 @@ int map_split_launch(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
     grid = grid < nb ? grid : nb;
     k_map_fused<DD, RT, FIN><<<grid, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes,
                                                         (const RT *)ctx->nodes_u, ctx->Jorb, pg,
-                                                        kc, ctx->cnt_dev, ctx->psum, tim, nb);
+                                                        kc, ctx->cnt_dev, ctx->psum, tim, nb, nr);
     return PIC_OK;
   }
   // FP32: the chunk's inputs staged in dynamic shared memory
@@ -517,24 +517,33 @@ int map_split_launch(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
     CK(cudaFuncSetAttribute(k_map_solve<DD, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             dsm));
   k_map_solve<DD, RT><<<nb, kPT, dsm, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes, pg, kc,
-                                                 ctx->cnt_dev, tim);
+                                                 ctx->cnt_dev, tim, nr);
   k_map_deposit<DD, RT, FIN><<<nb, kPT, 0, ctx->st>>>(pview<RT>(ctx), (const RT *)ctx->nodes,
                                                       (const RT *)ctx->nodes_u, ctx->Jorb, pg, kc,
-                                                      ctx->cnt_dev, ctx->psum, tim);
+                                                      ctx->cnt_dev, ctx->psum, tim, nr);
   return PIC_OK;
 }
 
 // The same for the FP32 stage of an FP64 context: FP32 arithmetic and FP32
 // node records on the FP64 particle storage.
 template <int DD, bool FIN>
-void map_split_launch_f32(pic_ctx *ctx, int nb, const PGeom &pg, const StepConst &sc,
+void map_split_launch_f32(pic_ctx *ctx, int nb, int nr, const PGeom &pg, const StepConst &sc,
                           unsigned long long *tim) {
   const KConst<float> kc = kconst<float>(sc, pg);
   k_map_solve<DD, float, double><<<nb, kPT, 0, ctx->st>>>(pview<double>(ctx), ctx->nodes_f, pg,
-                                                          kc, ctx->cnt_dev, tim);
+                                                          kc, ctx->cnt_dev, tim, nr);
   k_map_deposit<DD, float, FIN, double><<<nb, kPT, 0, ctx->st>>>(
       pview<double>(ctx), ctx->nodes_f, ctx->nodes_u_f, ctx->Jorb, pg, kc, ctx->cnt_dev,
-      ctx->psum, tim);
+      ctx->psum, tim, nr);
+}
+
+// Groups of kPT particles per chunk of the common-path map: as many as keep
+// at least two chunks per resident CTA slot (slots = CTAs per SM x SMs), at
+// most maxr, at least one.  Long chunks shorten the share of each chunk's
+// drain; short ones keep every SM busy on small problems.
+int chunk_groups(int64_t np, int maxr, int64_t slots) {
+  const int64_t r = np / ((int64_t)kPT * 2 * (slots > 0 ? slots : 1));
+  return (int)(r < 1 ? 1 : (r > maxr ? maxr : r));
 }
 
 int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
@@ -554,9 +563,14 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
     unsigned long long *tim = loop ? ctx->map_timer : nullptr;
     // the common path runs the lane-refill map over chunks of kChunkOf<RT>
     // particles; the general path one particle per thread
+    int nr = 1;
     if (!(sc_in.order != 2 || sc_in.refine_max > 0)) {
-      const int chunk = ctx->rsize == 8 && !ctx->eval_f32 ? kChunkOf<double> : kChunkOf<float>;
-      nb = (int)((ctx->np + chunk - 1) / chunk);
+      // resident CTAs per SM of the chunk kernels: 2 for FP64 (254
+      // registers), 4 for FP32 (128 registers)
+      const bool f64 = ctx->rsize == 8 && !ctx->eval_f32;
+      nr = chunk_groups(ctx->np, f64 ? kRefillOf<double> : kRefillOf<float>,
+                        (int64_t)(f64 ? 2 : 4) * ctx->num_sms);
+      nb = (int)((ctx->np + nr * kPT - 1) / (nr * kPT));
     }
 #define PIC_MAP_LAUNCH(FIN, GEN)                                                          \
   PIC_DISPATCH(ctx, (k_map<DD, RT, FIN, GEN><<<nb, kPT, 0, ctx->st>>>(                      \
@@ -565,11 +579,11 @@ int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
     // the common path: inner solves, then deposits (two launches)
     int e_split = PIC_OK;
 #define PIC_MAP_SPLIT(FIN) \
-  PIC_DISPATCH(ctx, (e_split = map_split_launch<DD, RT, FIN>(ctx, nb, pg, sc_in, tim)))
+  PIC_DISPATCH(ctx, (e_split = map_split_launch<DD, RT, FIN>(ctx, nb, nr, pg, sc_in, tim)))
     // the general kernels (degree-one shapes, refinement) only when needed
     const bool gen = sc_in.order != 2 || sc_in.refine_max > 0;
     if (ctx->eval_f32) {  // FP32 arithmetic on the FP64 particle storage
-#define PIC_MAP_F32(DD, FIN, GEN) map_split_launch_f32<DD, FIN>(ctx, nb, pg, sc_in, tim)
+#define PIC_MAP_F32(DD, FIN, GEN) map_split_launch_f32<DD, FIN>(ctx, nb, nr, pg, sc_in, tim)
 #define PIC_MAP_F32_D(FIN, GEN)                                                            \
   do {                                                                                     \
     if (ctx->g.dim == 1) PIC_MAP_F32(1, FIN, GEN);                                         \
