@@ -477,11 +477,7 @@ int enqueue_round(pic_ctx *ctx, const StepConst &sc, double tr, double ta, int f
   k_strial<<<sgrid(N3), kST, 0, ctx->st>>>(ctx->j, ctx->r, ctx->jt, ctx->dJ, ctx->dR, ctx->sctl,
                                            N3, ctx->opt.beta);
   KCHECK();
-  if ((e = field_real_to_complex(ctx, ctx->jt, ctx->jh, 3))) return e;
-  if ((e = fft_nd(ctx, ctx->jh, 3, -1))) return e;
-  if ((e = field_cn_update(ctx, ctx->jh, final_pass))) return e;
-  if ((e = field_pack_nodes(ctx, final_pass))) return e;
-  CK(cudaMemsetAsync(ctx->Jorb, 0, sizeof(double) * N3, ctx->st));
+  if ((e = field_evaluate(ctx, ctx->jt, final_pass))) return e;
   if ((e = particles_map_launch(ctx, sc, final_pass))) return e;
   if ((e = field_project_real(ctx, ctx->Jorb, ctx->Ht, 3))) return e;
   const int nb = sresid_blocks(ctx);

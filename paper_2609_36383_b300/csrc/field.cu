@@ -497,6 +497,14 @@ int finish_sum(pic_ctx *ctx, int nblk, double *host_out) {
   return PIC_OK;
 }
 
+// the queued form: the NQ sums land in dout[0 .. NQ) on the device
+template <int NQ>
+int queue_sum(pic_ctx *ctx, int nblk, double *dout) {
+  k_sum_partials<NQ><<<1, kThreads, 0, ctx->st>>>(ctx->red, nblk, dout);
+  KCHECK();
+  return PIC_OK;
+}
+
 inline int blocks(size_t n) { return (int)((n + kThreads - 1) / kThreads); }
 
 }  // namespace
@@ -640,6 +648,25 @@ int field_energy(pic_ctx *ctx, const double2 *phi_h, const double2 *A_h, const d
   return PIC_OK;
 }
 
+int field_energy_queued(pic_ctx *ctx, double *dout) {
+  int nb = blocks(ctx->g.Ng);
+  k_energy_parts<<<nb, kThreads, 0, ctx->st>>>(ctx->phi_h, ctx->A_h, ctx->U_h, spec_geom(ctx),
+                                               0.5 / ctx->opt.sigma1, 0.5 / ctx->opt.sigma2,
+                                               ctx->red);
+  KCHECK();
+  return queue_sum<1>(ctx, nb, dout);
+}
+
+int field_constraints_queued(pic_ctx *ctx, double *dout) {
+  int nb = blocks(ctx->g.Ng);
+  k_constraint_parts<<<nb, kThreads, 0, ctx->st>>>(ctx->phi_h, ctx->psi_h, ctx->rho_h, ctx->A_h,
+                                                   ctx->U_h, spec_geom(ctx), ctx->opt.sigma1,
+                                                   1.0 / (ctx->opt.kappa * ctx->opt.kappa),
+                                                   ctx->red);
+  KCHECK();
+  return queue_sum<2>(ctx, nb, dout);
+}
+
 int field_constraints(pic_ctx *ctx, double *gauss_rms, double *lorenz_rms) {
   int nb = blocks(ctx->g.Ng);
   k_constraint_parts<<<nb, kThreads, 0, ctx->st>>>(ctx->phi_h, ctx->psi_h, ctx->rho_h, ctx->A_h,
@@ -693,6 +720,14 @@ int field_mesh_work_real(pic_ctx *ctx, const double *H, double *work) {
 
 // mesh work sum_g J_orb . E^{1/2} dV of the last evaluation (Jorb_h holds the
 // projected transform of J_orb; phi1_h, U1_h the candidate n+1 potentials)
+int field_mesh_work_real_queued(pic_ctx *ctx, const double *H, double *dout) {
+  int nb = blocks(ctx->g.Ng);
+  k_mesh_work_real<<<nb, kThreads, 0, ctx->st>>>(H, ctx->work_h, ctx->g.Ng, ctx->g.dim,
+                                                 1.0 / ctx->g.Ng, ctx->red);
+  KCHECK();
+  return queue_sum<1>(ctx, nb, dout);
+}
+
 int field_mesh_work(pic_ctx *ctx, double *work) {
   int nb = blocks(ctx->g.Ng);
   k_mesh_work_parts<<<nb, kThreads, 0, ctx->st>>>(ctx->Jorb_h, ctx->phi_h, ctx->phi1_h,

@@ -670,6 +670,32 @@ int particles_commit(pic_ctx *ctx) {
   return PIC_OK;
 }
 
+// The same queued: the kinetic partials are copied to psum_host and merged
+// by particles_kinetic_collect after the caller's synchronisation.
+int particles_kinetic_queued(pic_ctx *ctx) {
+  if (ctx->np == 0) return PIC_OK;
+  PGeom pg = pgeom(ctx);
+  StepConst sc = base_sc(ctx);
+  int nb = nblk(ctx->np);
+  PIC_DISPATCH(ctx, (k_kinetic<DD, RT><<<nb, kPT, 0, ctx->st>>>(
+                         pview<RT>(ctx), A_typed<RT>(ctx), pg, kconst<RT>(sc, pg), ctx->psum)));
+  KCHECK();
+  k_psum_level2<<<kPsumBlocks, kPsumThreads, 0, ctx->st>>>(ctx->psum, nb, 1,
+                                                          ctx->psum + 2 * (size_t)nb);
+  KCHECK();
+  CK(cudaMemcpyAsync(ctx->psum_host, ctx->psum + 2 * (size_t)nb,
+                     sizeof(double) * 4 * kPsumBlocks, cudaMemcpyDeviceToHost, ctx->st));
+  return PIC_OK;
+}
+
+double particles_kinetic_collect(const pic_ctx *ctx) {
+  if (ctx->np == 0) return 0.0;
+  const double *ps = ctx->psum_host;
+  CSum k = csum_zero();
+  for (int b = 0; b < kPsumBlocks; b++) k = csum_merge(k, CSum{ps[4 * b], ps[4 * b + 1]});
+  return csum_value(k);
+}
+
 int particles_kinetic(pic_ctx *ctx, double *K) {
   if (ctx->np == 0) { *K = 0.0; return PIC_OK; }
   PGeom pg = pgeom(ctx);

@@ -66,7 +66,7 @@ void free_all(pic_ctx *ctx) {
                   ctx->Jorb_h, ctx->H, ctx->j, ctx->r, ctx->jt, ctx->Ht, ctx->rt, ctx->dir,
                   ctx->dJ, ctx->dR, ctx->tw[0], ctx->tw[1], ctx->tw[2], ctx->red, ctx->cnt_dev,
                   ctx->A_real_f, ctx->cnt_sort, ctx->keys, ctx->tmp_l, ctx->nodes_f,
-                  ctx->nodes_u_f};
+                  ctx->nodes_u_f, ctx->rep_dev};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->red_host) cudaFreeHost(ctx->red_host);
@@ -105,6 +105,7 @@ int alloc_mesh(pic_ctx *ctx) {
   size_t nred = 8 * (Ng / 256 + 2) + 1024 * 48 + 64;
   CK(cudaMalloc((void **)&ctx->red, R * nred));
   CK(cudaMallocHost((void **)&ctx->red_host, R * 64));
+  CK(cudaMalloc((void **)&ctx->rep_dev, R * 8));
   CK(cudaMalloc((void **)&ctx->cnt_dev, sizeof(EvalCounters)));
   CK(cudaMallocHost((void **)&ctx->cnt_host, sizeof(EvalCounters)));
   CK(cudaEventCreate(&ctx->ev0));
@@ -175,13 +176,8 @@ struct Tests {
 // for the device, so the sequence can be captured into a CUDA graph.
 int eval_enqueue(pic_ctx *ctx, const double *jdev, double *Hdev, double *rdev,
                  const StepConst &sc, int final_pass, double tr, double ta) {
-  const int Ng = ctx->g.Ng;
   int e;
-  if ((e = field_real_to_complex(ctx, jdev, ctx->jh, 3))) return e;
-  if ((e = fft_nd(ctx, ctx->jh, 3, -1))) return e;
-  if ((e = field_cn_update(ctx, ctx->jh, final_pass))) return e;
-  if ((e = field_pack_nodes(ctx, final_pass))) return e;
-  CK(cudaMemsetAsync(ctx->Jorb, 0, sizeof(double) * 3 * Ng, ctx->st));
+  if ((e = field_evaluate(ctx, jdev, final_pass))) return e;
   if ((e = particles_map_launch(ctx, sc, final_pass))) return e;
   // H = P J_orb with the real-space form of the Nyquist projector
   if ((e = field_project_real(ctx, ctx->Jorb, Hdev, 3))) return e;
@@ -917,9 +913,9 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
   ctx->j = j; ctx->H = H; ctx->r = r; ctx->jt = jt; ctx->Ht = Ht; ctx->rt = rt;
   if (status == PIC_OK) {
     TraceRange trace_c("commit");
-    double mesh_work;
-    if ((e = field_mesh_work_real(ctx, H, &mesh_work))) return e;
-    R.work_residual = ctx->dt * (ev.work_p - mesh_work);
+    // the commit and every commit-time sum are queued, then read back with
+    // one copy and one synchronisation
+    if ((e = field_mesh_work_real_queued(ctx, H, ctx->rep_dev))) return e;
     R.chain_rms = ctx->np ? std::sqrt(ev.chain / (3.0 * ctx->np)) : 0.0;
     R.inner_max = ev.cnt.inner_max;
     R.inner_mean = ctx->np ? (double)ev.cnt.inner_sum / ctx->np : 0.0;
@@ -934,7 +930,21 @@ int pic_step(pic_ctx *ctx, double tol, pic_report *out) {
     std::swap(ctx->A_real, ctx->A1_real);
     if ((e = particles_refresh_A(ctx))) return e;
     CK(cudaMemcpyAsync(ctx->J_acc, j, sizeof(double) * N3, cudaMemcpyDeviceToDevice, ctx->st));
-    if ((e = finish_report(ctx, &R))) return e;
+    if ((e = particles_kinetic_queued(ctx))) return e;
+    if ((e = field_energy_queued(ctx, ctx->rep_dev + 1))) return e;
+    if ((e = field_constraints_queued(ctx, ctx->rep_dev + 2))) return e;
+    CK(cudaMemcpyAsync(ctx->red_host, ctx->rep_dev, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                       ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    const double *rh = ctx->red_host;
+    R.work_residual = ctx->dt * (ev.work_p - rh[0] * ctx->g.dV);
+    R.K = particles_kinetic_collect(ctx);
+    // Parseval for the unnormalised DFT: sum_g |f_g|^2 = sum_k |f_k|^2 / Ng
+    R.W = rh[1] * ctx->g.dV / ctx->g.Ng;
+    R.E_tot = R.K + R.W;
+    R.gauss_rms = std::sqrt(rh[2]) / ctx->g.Ng;
+    R.lorenz_rms = std::sqrt(rh[3]) / ctx->g.Ng;
+    R.rel_dE = ctx->E0 != 0.0 ? (R.E_tot - ctx->E0) / ctx->E0 : 0.0;
     ctx->steps_done++;
     if (ctx->opt.sort_every > 0 && ctx->steps_done % ctx->opt.sort_every == 0 &&
         (e = particles_sort(ctx)))

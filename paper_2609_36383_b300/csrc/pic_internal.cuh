@@ -147,6 +147,7 @@ struct pic_ctx {
   // ---- reductions ------------------------------------------------------
   double *red;        // block partials
   double *red_host;   // pinned
+  double *rep_dev;    // 8 device slots of the queued commit-time sums
   EvalCounters *cnt_dev, *cnt_host;
   double *psum;       // per-block particle sums (work, chain, K)
   double *psum_host;  // pinned copy of the final-pass partials
@@ -241,6 +242,11 @@ int field_complex_to_real(pic_ctx *ctx, const double2 *src, double *dst, int nco
 int field_project_h(pic_ctx *ctx, double2 *f, int ncomp);
 int field_cn_update(pic_ctx *ctx, const double2 *jh, int want_uhalf);
 int field_pack_nodes(pic_ctx *ctx, int want_uhalf);
+// The whole spectral field step of one map evaluation at the trial current
+// jdev (real, 3Ng): transforms, projection, continuity and CN update into the
+// candidate spectra, gather records (final pass: with U^{n+1/2}), and J_orb
+// cleared for the deposit.  Fused launches on 2D meshes (field2d.cu).
+int field_evaluate(pic_ctx *ctx, const double *jdev, int final_pass);
 int field_initial_constraints(pic_ctx *ctx);
 // The CN update from any field state `in` into `out` and the gather spectra
 // `spec`; the update is linear in (j, state) jointly, so a tangent state and a
@@ -282,6 +288,12 @@ int field_mesh_work(pic_ctx *ctx, double *work);
 // Nyquist projection of ncomp real mesh arrays (src may equal dst)
 int field_project_real(pic_ctx *ctx, const double *src, double *dst, int ncomp);
 int field_mesh_work_real(pic_ctx *ctx, const double *H, double *work);
+// Queued forms of the commit-time sums (no synchronisation): raw sums into
+// device slots (energy: 1, constraints: 2, mesh work: 1), scaled by the
+// caller after one copy and one synchronisation for all of them.
+int field_energy_queued(pic_ctx *ctx, double *dout);
+int field_constraints_queued(pic_ctx *ctx, double *dout);
+int field_mesh_work_real_queued(pic_ctx *ctx, const double *H, double *dout);
 
 // ---------------------------------------------------------------- particle.cu
 int particles_alloc(pic_ctx *ctx, int64_t n);
@@ -298,6 +310,8 @@ int particles_map_finish(pic_ctx *ctx, double *work_sum, double *chain_sum, Eval
 void particles_final_sums(const pic_ctx *ctx, double *work, double *chain);
 int particles_commit(pic_ctx *ctx);
 int particles_kinetic(pic_ctx *ctx, double *K);
+int particles_kinetic_queued(pic_ctx *ctx);           // partials to psum_host, no sync
+double particles_kinetic_collect(const pic_ctx *ctx);  // after the caller's sync
 // refresh the particle-precision copy of A^n after A_real changed
 int particles_refresh_A(pic_ctx *ctx);
 int particles_export(pic_ctx *ctx, double *x, double *P, double *w, int32_t *sp,
