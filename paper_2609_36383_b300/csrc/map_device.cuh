@@ -930,6 +930,9 @@ struct PView {
   const int32_t *sp;
   T *vbar, *Pnew;
   int32_t *iters;
+  // FP32 contexts: each converged particle's deposit record (two float4 per
+  // particle, DepRec), written by the solve pass for the deposit pass; or null
+  float4 *drec = nullptr;
 };
 
 // sums of NQ values over the CTA, written to out[0 .. NQ)
@@ -1740,6 +1743,31 @@ __device__ __forceinline__ bool stage_chunk(const PView<S> &pv, const S *__restr
   return true;
 }
 
+// The deposit record of one particle, written by the FP32 solve pass when the
+// particle's inner solve ends and read by the deposit pass as two coalesced
+// 16-byte loads: [cell x | cell y << 16 (int bits), offset x, offset y,
+// crossing class (int bits: 0, 1, 2 knot planes or more; 3 = failed)] and
+// [orbit velocity (3), charge q].
+template <int D>
+__device__ __forceinline__ void drec_write(float4 *rec, const LaneSolve<D, float> &ls, int cls) {
+  const int cpk = ls.cell[0] | (D > 1 ? (ls.cell[1] << 16) : 0);
+  rec[0] = make_float4(__int_as_float(cpk), ls.off[0], D > 1 ? ls.off[1] : 0.0f,
+                       __int_as_float(cls));
+  rec[1] = make_float4(ls.vb[0], ls.vb[1], ls.vb[2], ls.pc.q);
+}
+
+// the number of knot planes (capped at 2) the orbit from off with velocity vb crosses
+template <int D, typename T>
+__device__ __forceinline__ int crossing_class(const T off[3], const T vb[3], const T dtdx[3]) {
+  int cls = 0;
+#pragma unroll
+  for (int l = 0; l < D; l++) {
+    const T u = off[l] + vb[l] * dtdx[l];
+    cls += (u >= T(0.5) || u < T(-0.5)) ? 1 : 0;
+  }
+  return cls < 2 ? cls : 2;
+}
+
 // The inner solves of the particle map over one chunk of nr * kPT particle
 // slots (nr <= kRefillOf<T>) starting at c0 (the common path: quadratic
 // shapes, no refinement):
@@ -1795,6 +1823,10 @@ __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_
           pv.Pnew[c * cap + i] = (S)ls.Pn1[c];
         }
         pv.iters[i] = r == 1 ? ls.it : -1;
+        if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value && D < 3) {
+          if (pv.drec)
+            drec_write<D>(pv.drec + 2 * i, ls, r == 1 ? crossing_class<D, T>(ls.off, ls.vb, ls.dtdx) : 3);
+        }
         if (r == 1) {
           it_sum += (unsigned)ls.it;
           mx_it = ls.it > mx_it ? ls.it : mx_it;
@@ -1824,26 +1856,43 @@ __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_
   }
 }
 
-// What the deposit of one particle reads: position, orbit velocity, weight
-// and species.
+// What the deposit of one particle reads: position, orbit velocity, charge.
 template <typename T>
 struct DepIn {
   int cell[3];
   T off[3], vb[3];
-  double w;
-  int sp;
+  T q;
 };
 
+// from the particle arrays, or (rec non-null) from the particle's deposit
+// record (drec_write)
 template <int D, typename T, typename S>
-__device__ __forceinline__ void dep_load(DepIn<T> &o, const PView<S> &pv, int64_t i) {
+__device__ __forceinline__ void dep_load(DepIn<T> &o, const PView<S> &pv, int64_t i,
+                                         const KConst<T> &kc, const float4 *rec) {
+  if (rec) {
+    const float4 a = rec[2 * i], b = rec[2 * i + 1];
+    const int cpk = __float_as_int(a.x);
+    o.cell[0] = D > 1 ? (cpk & 0xffff) : cpk;
+    o.cell[1] = D > 1 ? (cpk >> 16) : 0;
+    o.cell[2] = 0;
+    o.off[0] = (T)a.y;
+    o.off[1] = (T)a.z;
+    o.off[2] = T(0);
+    o.vb[0] = (T)b.x;
+    o.vb[1] = (T)b.y;
+    o.vb[2] = (T)b.z;
+    o.q = (T)b.w;
+    return;
+  }
 #pragma unroll
   for (int l = 0; l < 3; l++) {
     o.cell[l] = l < D ? pv.cell[l * pv.cap + i] : 0;
     o.off[l] = l < D ? (T)pv.off[l * pv.cap + i] : T(0);
     o.vb[l] = (T)pv.vbar[l * pv.cap + i];
   }
-  o.w = pv.w[i];
-  o.sp = pv.sp[i];
+  const int s_id = pv.sp[i];
+  if constexpr (std::is_same<T, float>::value) o.q = (float)pv.w[i] * kc.qT[s_id];
+  else o.q = (T)(pv.w[i] * kc.qs[s_id]);
 }
 
 // The orbit deposits of one chunk from the stored orbit velocities (Eq.
@@ -1877,12 +1926,16 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
     __shared__ T s_win[(kPT / 32) * WarpWin<D>::NE * 32];
     __shared__ short s_dord[kPT / 32][R];
     const int r0 = wid * nr * 32;  // this warp's range: nr rounds of 32
+    // plain passes read the deposit records the solve pass wrote, if any
+    const float4 *rec = FINAL ? nullptr : pv.drec;
     int cls_q[kRefillOf<T>];
 #pragma unroll
     for (int q = 0; q < kRefillOf<T>; q++) {
       const int k = r0 + q * 32 + lane;
       int cls = 3;  // empty slot, failed particle, or a round past nr: last
-      if (q < nr && k < nvalid && pv.iters[c0 + k] > 0) {
+      if (rec) {
+        if (q < nr && k < nvalid) cls = __float_as_int(rec[2 * (c0 + k)].w);
+      } else if (q < nr && k < nvalid && pv.iters[c0 + k] > 0) {
         const int64_t i = c0 + k;
         cls = 0;
 #pragma unroll
@@ -1929,14 +1982,14 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
     // (slot -1: an empty slot or a failed particle)
     DepIn<T> cur, nxt;
     int kcur = s_dord[wid][lane];
-    if (kcur >= 0) dep_load<D, T, S>(cur, pv, c0 + r0 + kcur);
+    if (kcur >= 0) dep_load<D, T, S>(cur, pv, c0 + r0 + kcur, kc, rec);
     T dtdx[3];
 #pragma unroll
     for (int l = 0; l < 3; l++) dtdx[l] = l < D ? kc.dt * ms.inv_dx[l] : T(0);
 #pragma unroll 1
     for (int q = 0; q < nr; q++) {
       const int knx = q + 1 < nr ? s_dord[wid][(q + 1) * 32 + lane] : -1;
-      if (knx >= 0) dep_load<D, T, S>(nxt, pv, c0 + r0 + knx);
+      if (knx >= 0) dep_load<D, T, S>(nxt, pv, c0 + r0 + knx, kc, rec);
       if (kcur >= 0) {
         PushConst<T> pc;
         if (FINAL) {  // the work and chain-rule sums need the push constants
@@ -1944,7 +1997,7 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
           lane_init<D, T, S>(d, pv, c0 + r0 + kcur, kc, ms);
           pc = d.pc;
         } else {
-          pc.q = (T)cur.w * kc.qT[cur.sp];
+          pc.q = cur.q;
         }
         deposit_orbit<D, T, FINAL, false>(pc, cur.cell, cur.off, dtdx, T(0), T(1), kc.dt, T(1),
                                           cur.vb, nodes, nodes_u, J, pg, kc, ms, win_col, ref,

@@ -335,6 +335,7 @@ PView<T> pview(pic_ctx *ctx) {
   v.vbar = (T *)ctx->vbar;
   v.Pnew = (T *)ctx->Pnew;
   v.iters = ctx->iters;
+  v.drec = ctx->dep_rec;
   return v;
 }
 
@@ -375,7 +376,7 @@ int particles_alloc(pic_ctx *ctx, int64_t n) {
                    (void **)&ctx->id, &ctx->Am, &ctx->v0, &ctx->vbar, &ctx->Pnew,
                    (void **)&ctx->iters, (void **)&ctx->u_in, (void **)&ctx->tmp_d,
                    (void **)&ctx->tmp_i, (void **)&ctx->psum, (void **)&ctx->keys,
-                   (void **)&ctx->tmp_l};
+                   (void **)&ctx->tmp_l, (void **)&ctx->dep_rec};
   for (void **b : bufs) {
     if (*b) cudaFree(*b);
     *b = nullptr;
@@ -396,6 +397,7 @@ int particles_alloc(pic_ctx *ctx, int64_t n) {
   CK(cudaMalloc(&ctx->vbar, R * 3 * cap));
   CK(cudaMalloc(&ctx->Pnew, R * 3 * cap));
   CK(cudaMalloc((void **)&ctx->iters, sizeof(int32_t) * cap));
+  if (R == 4) CK(cudaMalloc((void **)&ctx->dep_rec, 2 * sizeof(float4) * cap));
   CK(cudaMalloc((void **)&ctx->u_in, sizeof(double) * 3 * cap));
   CK(cudaMalloc((void **)&ctx->tmp_d, sizeof(double) * 7 * cap));
   CK(cudaMalloc((void **)&ctx->tmp_i, sizeof(int32_t) * 4 * cap));

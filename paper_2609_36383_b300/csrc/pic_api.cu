@@ -66,7 +66,7 @@ void free_all(pic_ctx *ctx) {
                   ctx->Jorb_h, ctx->H, ctx->j, ctx->r, ctx->jt, ctx->Ht, ctx->rt, ctx->dir,
                   ctx->dJ, ctx->dR, ctx->tw[0], ctx->tw[1], ctx->tw[2], ctx->red, ctx->cnt_dev,
                   ctx->A_real_f, ctx->cnt_sort, ctx->keys, ctx->tmp_l, ctx->nodes_f,
-                  ctx->nodes_u_f, ctx->rep_dev};
+                  ctx->nodes_u_f, ctx->rep_dev, ctx->dep_rec};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ctx->red_host) cudaFreeHost(ctx->red_host);

@@ -111,6 +111,7 @@ struct pic_ctx {
   int64_t *id;        // [cap] load order index
   void *Am, *v0, *vbar, *Pnew;  // [3][cap] step work
   int32_t *iters;     // [cap]
+  float4 *dep_rec;    // [2 cap] deposit records of the FP32 map (mixed contexts), or null
   double *u_in;       // [3][cap] mechanical input awaiting pic_start
   // sort scratch
   int32_t *keys;      // [cap] sort keys
