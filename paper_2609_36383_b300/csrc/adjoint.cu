@@ -153,8 +153,11 @@ __global__ void k_vjp_scatter(PView<double> pv, const double *__restrict__ nodes
   const PushConst<Dual> pd = dual_push_const(pc);
   double gphi0[3], Dm0[3][3], Ap0[3];
   int np2 = 0;
-  orbit_gather<D, double, false>(cell, off, dtdx, 0.0, 1.0, nodes, pg, kc, ms, vb, gphi0, Dm0,
-                                 Ap0, np2, 2);
+  // an orbit too long for the walk was flagged by the first pass (and no
+  // pass after it runs then); never use gathered values it did not write
+  if (!orbit_gather<D, double, false>(cell, off, dtdx, 0.0, 1.0, nodes, pg, kc, ms, vb, gphi0,
+                                      Dm0, Ap0, np2, 2))
+    return;
   Dual vbc[3];
   for (int l = 0; l < 3; l++) vbc[l] = Dual(vb[l]);
   double ggphi[3] = {0.0, 0.0, 0.0}, gDm[3][3] = {{0.0}}, gAp[3] = {0.0, 0.0, 0.0};

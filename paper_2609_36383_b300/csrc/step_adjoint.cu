@@ -304,7 +304,9 @@ struct SadjParticle {
   int cell[3];
   double off[3], dtdx[3], vb[3], mu[3], Pb[3];
   double gphi0[3], Dm0[3][3], Ap0[3];
-  __device__ void load(const PView<double> &pv, int64_t i, const double *__restrict__ nodes,
+  // false when the orbit is too long for the walk (flagged by the first pass,
+  // after which no later pass runs): the gathered values are then not set
+  __device__ bool load(const PView<double> &pv, int64_t i, const double *__restrict__ nodes,
                        const PGeom &pg, const KConst<double> &kc, const MapScale<double> &ms,
                        const double *__restrict__ vb_in, const double *__restrict__ mu_in,
                        const double *__restrict__ Pb1) {
@@ -316,8 +318,8 @@ struct SadjParticle {
       Pb[c] = Pb1 ? Pb1[c * cap + i] : 0.0;
     }
     int np2 = 0;
-    orbit_gather<D, double, false>(cell, off, dtdx, 0.0, 1.0, nodes, pg, kc, ms, vb, gphi0, Dm0,
-                                   Ap0, np2, 2);
+    return orbit_gather<D, double, false>(cell, off, dtdx, 0.0, 1.0, nodes, pg, kc, ms, vb, gphi0,
+                                          Dm0, Ap0, np2, 2);
   }
 };
 
@@ -335,7 +337,7 @@ __global__ void k_sadj_records(PView<double> pv, const double *__restrict__ node
   if (i >= pv.np || cnt->status) return;
   const MapScale<double> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   SadjParticle<D> sp;
-  sp.load(pv, i, nodes, pg, kc, ms, vb_in, mu_in, Pb1);
+  if (!sp.load(pv, i, nodes, pg, kc, ms, vb_in, mu_in, Pb1)) return;
   const PushConst<Dual> pd0 = dual_push_const(sp.pc);
   double ggphi[3] = {0.0, 0.0, 0.0}, gDm[3][3] = {{0.0}}, gAp[3] = {0.0, 0.0, 0.0};
   const int nin = D + 3 * D + 3;  // grad phi (D), D_i A (3 x D), A^{n+1} (3)
@@ -389,7 +391,7 @@ __global__ void k_sadj_momentum(PView<double> pv, const double *__restrict__ nod
   if (i >= pv.np || cnt->status) return;
   const MapScale<double> ms = {{kc.inv_dx[0], kc.inv_dx[1], kc.inv_dx[2]}, kc.inv_dV};
   SadjParticle<D> sp;
-  sp.load(pv, i, nodes, pg, kc, ms, vb_in, mu_in, Pb1);
+  if (!sp.load(pv, i, nodes, pg, kc, ms, vb_in, mu_in, Pb1)) return;
   const PushConst<double> &pc = sp.pc;
   const PushConst<Dual> pd0 = dual_push_const(pc);
   const double ik2 = pc.inv_mk * pc.inv_mk;
@@ -460,8 +462,9 @@ __global__ void k_sadj_position(PView<double> pv, const double *__restrict__ nod
     for (int m = 0; m < 3; m++) offd[m] = Dual(off[m], m == l ? 1.0 : 0.0);
     Dual gphi[3], Dm[3][3], Ap[3], vn[3], Pc[3];
     int np_ = 0;
-    orbit_gather<D, Dual, false>(cell, offd, dtdxd, Dual(0.0), Dual(1.0), dnodes, pg, kcd, msd,
-                                 vbd, gphi, Dm, Ap, np_, 2);
+    if (!orbit_gather<D, Dual, false>(cell, offd, dtdxd, Dual(0.0), Dual(1.0), dnodes, pg, kcd,
+                                      msd, vbd, gphi, Dm, Ap, np_, 2))
+      return;  // flagged by the first pass, as in SadjParticle::load
     gmhc_push<D, Dual>(pd, Ap, gphi, Dm, vbd, vn, Pc);
     double val = 0.0;
     for (int c = 0; c < 3; c++) val += mu[c] * vn[c].d + Pb[c] * Pc[c].d;
