@@ -331,3 +331,33 @@ def test_mixed_precision_bounded_against_fp64_oracle():
         r = s.step(1e-10)
         assert r["status"] == 0
         assert abs(r["rel_dE"]) < 1e-6
+
+
+def test_full_size_mixed_sampled_parity():
+    """The FP32-mixed map at full size (128^2 mesh, 1,048,576 particles) in the
+    launch configuration the benchmark times: 512-particle chunks whose inputs
+    are staged in shared memory, and deposits from the records the solve pass
+    writes.  Sampled orbit velocities and momenta against the oracle's FP64
+    inner solves at the same trial current, the deposited current against the
+    FP64 GPU path (itself checked against the oracle above), at the FP32
+    bounds of the small mixed case."""
+    cfg = pic_inputs.weibel_2d()
+    o = make_oracle(cfg)
+    o.start()
+    J = o.fields()["J"]
+    s64 = make_gpu(cfg)
+    s64.start()
+    st64, H64, _, _, _ = s64.eval_map(J, 1e-14)
+    s64.close()
+    s32 = make_gpu(cfg, precision=1)
+    s32.start()
+    st32, H32, v32, P32, _ = s32.eval_map(J, 1e-14)
+    s32.close()
+    assert st64 == 0 and st32 == 0
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(cfg["w"].shape[0], 512, replace=False))
+    st_o, vo, Po, _ = o.eval_particles(J, 1e-14, idx)
+    assert st_o == 0
+    assert rel_err(v32[:, idx], vo) < 2e-6
+    assert rel_err(P32[:, idx], Po) < 2e-6
+    assert scaled_err(H32, H64, gross_scales(cfg)["H"]) < 2e-6
