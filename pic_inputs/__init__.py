@@ -228,16 +228,19 @@ def thermal_box(dim=3, n=8, ppc=2, T=0.05, u_drift=0.3, dt=0.1, tol=1e-12, seed=
     """Counter-streaming Maxwell-Juettner beams along z in a periodic box of
     any dimension (used for parity checks in 1D-3D): uniform random positions
     per cell, `ppc` particles per cell split between the beams, a random
-    vector-potential seed of amplitude `noise` on every node."""
+    vector-potential seed of amplitude `noise` on every node.  `n` is the
+    node count of every axis, or a sequence of one count per axis (a box of
+    side L on every axis, so the cells are not square then)."""
     rng = np.random.default_rng(seed)
-    ns = [n] * dim
+    ns = [int(v) for v in n] if hasattr(n, "__len__") else [n] * dim
+    assert len(ns) == dim
     Ls = [L] * dim
     x0 = [-0.5 * L] * dim
-    ncell = n ** dim
+    ncell = int(np.prod(ns))
     cells = np.repeat(np.arange(ncell), ppc)
     N = cells.shape[0]
     idx = np.stack(np.unravel_index(cells, ns[::-1])[::-1])  # x fastest
-    x = np.stack([x0[l] + (idx[l] + rng.random(N)) * Ls[l] / n for l in range(dim)])
+    x = np.stack([x0[l] + (idx[l] + rng.random(N)) * Ls[l] / ns[l] for l in range(dim)])
     half = N // 2
     u = np.concatenate([drifting_mj(rng, T, u_drift, 2, half),
                         drifting_mj(rng, T, -u_drift, 2, N - half)], axis=1)
@@ -245,7 +248,8 @@ def thermal_box(dim=3, n=8, ppc=2, T=0.05, u_drift=0.3, dt=0.1, tol=1e-12, seed=
     u = u[:, perm]
     w = np.full(N, float(np.prod(Ls)) / N)
     A = noise * rng.standard_normal((3, ncell))
-    return dict(name=f"thermal_box_{dim}d_{n}_{ppc}ppc", dim=dim, n=ns, L=Ls, x0=x0,
+    return dict(name=f"thermal_box_{dim}d_{'x'.join(map(str, ns))}_{ppc}ppc", dim=dim, n=ns,
+                L=Ls, x0=x0,
                 species=[(-1.0, 1.0)], rho_bg=1.0, dt=dt, tol=tol, steps=4,
                 x=x, u=u, w=w, sp=np.zeros(N, np.int32), A=A, U=None)
 

@@ -66,6 +66,12 @@ def _thermal_3d():
     return pic_inputs.thermal_box(dim=3, n=8, ppc=2, T=0.05, u_drift=0.3, dt=0.2, seed=4)
 
 
+def _rect_2d():
+    # a rectangular mesh (32 x 8 nodes, rectangular cells): rows and columns of
+    # the 2D field step differ in length
+    return pic_inputs.thermal_box(dim=2, n=(32, 8), ppc=6, T=0.05, u_drift=0.4, dt=0.2, seed=6)
+
+
 CASES = {
     "1d_two_stream": small_1d,
     "3d_thermal": _thermal_3d,
@@ -73,6 +79,7 @@ CASES = {
     "2d_ragged_knots": _ragged_2d,
     "2d_fast_multicross": _fast_2d,
     "2d_two_species": _two_species_2d,
+    "2d_rect_32x8": _rect_2d,
 }
 
 
