@@ -1444,6 +1444,7 @@ template <typename T>
 constexpr int kChunkOf = kRefillOf<T> * kPT;
 constexpr int kChunk = kChunkOf<float>;        // the FP32 staging chunk
 constexpr int kChunkMax = kChunkOf<double>;    // the longest chunk
+static_assert(kChunkMax % kChunk == 0, "the staging chunk divides the capacity granule");
 
 // one particle's inner solve between sweeps
 template <int D, typename T>
@@ -1789,6 +1790,9 @@ __device__ __forceinline__ void map_chunk_solve(const PView<S> &pv, const int64_
   const int nvalid = nvalid64 < chunk ? (int)nvalid64 : chunk;
   if (threadIdx.x == 0) s_next = 0;
   const S *vel = kc.warm ? pv.vbar : pv.v0;
+  // a chunk that would reach past the arrays (never, with the host's choice
+  // of chunk length) reads them in place instead
+  if (stg && c0 + chunk > pv.cap) stg = nullptr;
   if (stg) {
     if (!stage_chunk<D, S>(pv, vel, c0, chunk, stg, bar, cnt)) return;
     // 1. order the chunk by predicted crossing class

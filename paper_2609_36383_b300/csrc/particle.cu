@@ -541,11 +541,15 @@ void map_split_launch_f32(pic_ctx *ctx, int nb, int nr, const PGeom &pg, const S
 
 // Groups of kPT particles per chunk of the common-path map: as many as keep
 // at least two chunks per resident CTA slot (slots = CTAs per SM x SMs), at
-// most maxr, at least one.  Long chunks shorten the share of each chunk's
-// drain; short ones keep every SM busy on small problems.
+// most maxr, at least one, and a power of two: the chunk then divides the
+// capacity granule kChunkMax, so a chunk's staging copies never read past
+// the particle arrays.  Long chunks shorten the share of each chunk's drain;
+// short ones keep every SM busy on small problems.
 int chunk_groups(int64_t np, int maxr, int64_t slots) {
   const int64_t r = np / ((int64_t)kPT * 2 * (slots > 0 ? slots : 1));
-  return (int)(r < 1 ? 1 : (r > maxr ? maxr : r));
+  int g = 1;
+  while (2 * g <= maxr && 2 * g <= r) g *= 2;
+  return g;
 }
 
 int particles_map_launch(pic_ctx *ctx, const StepConst &sc_in, int final_pass) {
