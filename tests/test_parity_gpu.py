@@ -347,8 +347,14 @@ def test_full_size_mixed_sampled_parity():
     writes.  Sampled orbit velocities and momenta against the oracle's FP64
     inner solves at the same trial current, the deposited current against the
     FP64 GPU path (itself checked against the oracle above), at the FP32
-    bounds of the small mixed case."""
+    bounds of the small mixed case.  333 particles are left out, so the last
+    chunk of each launch is ragged."""
     cfg = pic_inputs.weibel_2d()
+    keep = cfg["w"].shape[0] - 333
+    for k in ("x", "u"):
+        cfg[k] = cfg[k][:, :keep]
+    cfg["w"] = cfg["w"][:keep]
+    cfg["sp"] = cfg["sp"][:keep]
     o = make_oracle(cfg)
     o.start()
     J = o.fields()["J"]
