@@ -502,6 +502,38 @@ __device__ __forceinline__ void accumulate_slab(const KConst<T> &kc, const T off
   }
 }
 
+// One node's terms of the discrete gradient (node units), for the NC
+// columns j with orbit integrals wd[j] = int dS/du_j and w1[j] = int s dS/du_j:
+//   Dm[c][j] += A^n_c wd[j] + (A^{n+1}_c - A^n_c) w1[j]
+// evaluated as A^n_c (wd[j] - w1[j]) + A^{n+1}_c w1[j], two FMAs per term
+// (r: the node record, A^n at r[D + c], A^{n+1} at r[D + 3 + c]).  On a
+// substep (SUB) the potential is A^n + (ta + s tsp) (A^{n+1} - A^n).
+template <int NC, int D, typename T, bool SUB>
+__device__ __forceinline__ void dgrad_node(T (&Dm)[3][3], const T *r, const T (&wd)[NC],
+                                           const T (&w1)[NC], T ta, T tsp) {
+  if (SUB) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      T An = r[D + c], dA = r[D + 3 + c] - An;
+      An += ta * dA;
+      dA *= tsp;
+#pragma unroll
+      for (int j = 0; j < NC; j++) Dm[c][j] += An * wd[j] + dA * w1[j];
+    }
+    return;
+  }
+  T wm[NC];
+#pragma unroll
+  for (int j = 0; j < NC; j++) wm[j] = wd[j] - w1[j];
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int j = 0; j < NC; j++) {
+      Dm[c][j] += r[D + c] * wm[j];
+      Dm[c][j] += r[D + 3 + c] * w1[j];
+    }
+}
+
 // Inner-iteration gather: grad phi-bar (Eq. orbit-gather-general with
 // G = grad phi^{1/2}) and the discrete gradient D (3 x D, node units until
 // the caller scales column j by 1/dx_j).
@@ -540,17 +572,9 @@ struct GatherOrbit {
             load_rec<NVP>(nodes + (size_t)g * NVP, r);
 #pragma unroll
             for (int c = 0; c < D; c++) gphi[c] += r[c] * pa.Sb[k];
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-              T An = r[D + c], dA = r[D + 3 + c] - An;
-              if (SUB) {
-                An += ta * dA;
-                dA *= tsp;
-              }
-              Dm[c][0] += An * pa.Wd[0][k] + dA * pa.W1[0][k];
-              Dm[c][1] += An * pa.Wd[1][k] + dA * pa.W1[1][k];
-              Dm[c][D > 2 ? 2 : 0] += An * Wz[k] + dA * W1z[k];
-            }
+            const T wd[3] = {pa.Wd[0][k], pa.Wd[1][k], Wz[k]};
+            const T w1[3] = {pa.W1[0][k], pa.W1[1][k], W1z[k]};
+            dgrad_node<3, D, T, SUB>(Dm, r, wd, w1, ta, tsp);
           }
       }
       return;
@@ -569,16 +593,13 @@ struct GatherOrbit {
           load_rec<NVP>(nodes + (size_t)g * NVP, r);
 #pragma unroll
           for (int c = 0; c < D; c++) gphi[c] += r[c] * pa.Sb[k];
+          T wd[D], w1[D];
 #pragma unroll
-          for (int c = 0; c < 3; c++) {
-            T An = r[D + c], dA = r[D + 3 + c] - An;
-            if (SUB) {
-              An += ta * dA;
-              dA *= tsp;
-            }
-#pragma unroll
-            for (int j = 0; j < D; j++) Dm[c][j] += An * pa.Wd[j][k] + dA * pa.W1[j][k];
+          for (int j = 0; j < D; j++) {
+            wd[j] = pa.Wd[j][k];
+            w1[j] = pa.W1[j][k];
           }
+          dgrad_node<D, D, T, SUB>(Dm, r, wd, w1, ta, tsp);
         }
   }
 };
@@ -644,17 +665,10 @@ struct DepositOrbit {
 #pragma unroll
               for (int c = 0; c < D; c++) gphi[c] += r[c] * pa.Sb[k];
 #pragma unroll
-              for (int c = 0; c < 3; c++) {
-                Ubar[c] += u[c] * pa.Sb[k];
-                T An = r[D + c], dA = r[D + 3 + c] - An;
-                if (SUB) {
-                  An += ta * dA;
-                  dA *= tsp;
-                }
-                Dm[c][0] += An * pa.Wd[0][k] + dA * pa.W1[0][k];
-                Dm[c][1] += An * pa.Wd[1][k] + dA * pa.W1[1][k];
-                Dm[c][D > 2 ? 2 : 0] += An * Wz[k] + dA * W1z[k];
-              }
+              for (int c = 0; c < 3; c++) Ubar[c] += u[c] * pa.Sb[k];
+              const T wd[3] = {pa.Wd[0][k], pa.Wd[1][k], Wz[k]};
+              const T w1[3] = {pa.W1[0][k], pa.W1[1][k], W1z[k]};
+              dgrad_node<3, D, T, SUB>(Dm, r, wd, w1, ta, tsp);
             }
 #pragma unroll
             for (int c = 0; c < 3; c++)
@@ -680,16 +694,14 @@ struct DepositOrbit {
 #pragma unroll
             for (int c = 0; c < D; c++) gphi[c] += r[c] * pa.Sb[k];
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-              Ubar[c] += u[c] * pa.Sb[k];
-              T An = r[D + c], dA = r[D + 3 + c] - An;
-              if (SUB) {
-                An += ta * dA;
-                dA *= tsp;
-              }
+            for (int c = 0; c < 3; c++) Ubar[c] += u[c] * pa.Sb[k];
+            T wd[D], w1[D];
 #pragma unroll
-              for (int j = 0; j < D; j++) Dm[c][j] += An * pa.Wd[j][k] + dA * pa.W1[j][k];
+            for (int j = 0; j < D; j++) {
+              wd[j] = pa.Wd[j][k];
+              w1[j] = pa.W1[j][k];
             }
+            dgrad_node<D, D, T, SUB>(Dm, r, wd, w1, ta, tsp);
           }
     }
     // window coordinates of the piece's base node (relative to ref)
