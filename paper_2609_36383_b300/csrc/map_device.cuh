@@ -1880,24 +1880,29 @@ struct DepIn {
   T q;
 };
 
+// the deposit inputs held by one deposit record (drec_write)
+template <int D, typename T>
+__device__ __forceinline__ void dep_from_rec(DepIn<T> &o, const float4 a, const float4 b) {
+  const int cpk = __float_as_int(a.x);
+  o.cell[0] = D > 1 ? (cpk & 0xffff) : cpk;
+  o.cell[1] = D > 1 ? (cpk >> 16) : 0;
+  o.cell[2] = 0;
+  o.off[0] = (T)a.y;
+  o.off[1] = (T)a.z;
+  o.off[2] = T(0);
+  o.vb[0] = (T)b.x;
+  o.vb[1] = (T)b.y;
+  o.vb[2] = (T)b.z;
+  o.q = (T)b.w;
+}
+
 // from the particle arrays, or (rec non-null) from the particle's deposit
 // record (drec_write)
 template <int D, typename T, typename S>
 __device__ __forceinline__ void dep_load(DepIn<T> &o, const PView<S> &pv, int64_t i,
                                          const KConst<T> &kc, const float4 *rec) {
   if (rec) {
-    const float4 a = rec[2 * i], b = rec[2 * i + 1];
-    const int cpk = __float_as_int(a.x);
-    o.cell[0] = D > 1 ? (cpk & 0xffff) : cpk;
-    o.cell[1] = D > 1 ? (cpk >> 16) : 0;
-    o.cell[2] = 0;
-    o.off[0] = (T)a.y;
-    o.off[1] = (T)a.z;
-    o.off[2] = T(0);
-    o.vb[0] = (T)b.x;
-    o.vb[1] = (T)b.y;
-    o.vb[2] = (T)b.z;
-    o.q = (T)b.w;
+    dep_from_rec<D, T>(o, rec[2 * i], rec[2 * i + 1]);
     return;
   }
 #pragma unroll
@@ -1994,14 +1999,52 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
     T *win_col = win_warp + lane;
     for (int e = 0; e < WarpWin<D>::NE; e++) win_col[e * 32] = T(0);
     __syncwarp();
+    T dtdx[3];
+#pragma unroll
+    for (int l = 0; l < 3; l++) dtdx[l] = l < D ? kc.dt * ms.inv_dx[l] : T(0);
+    if constexpr (!FINAL && std::is_same<S, float>::value) {
+      // plain passes of FP32 contexts (their records always exist): every
+      // round's record is loaded up front, in the class order, so that the
+      // range's loads are in flight together (slot -1: an empty slot or a
+      // failed particle)
+      constexpr int Q = kRefillOf<T>;
+      float4 ra[Q], rb[Q];
+      int kq[Q];
+#pragma unroll
+      for (int q = 0; q < Q; q++) {
+        kq[q] = q < nr ? s_dord[wid][q * 32 + lane] : -1;
+        if (kq[q] >= 0) {
+          const int64_t i = c0 + r0 + kq[q];
+          ra[q] = rec[2 * i];
+          rb[q] = rec[2 * i + 1];
+        }
+      }
+#pragma unroll 1
+      for (int q = 0; q < nr; q++) {
+        const float4 a = ra[0], b = rb[0];
+        const int k0 = kq[0];
+#pragma unroll
+        for (int t = 0; t + 1 < Q; t++) {
+          ra[t] = ra[t + 1];
+          rb[t] = rb[t + 1];
+          kq[t] = kq[t + 1];
+        }
+        if (k0 >= 0) {
+          DepIn<T> cur;
+          dep_from_rec<D, T>(cur, a, b);
+          PushConst<T> pc;
+          pc.q = cur.q;
+          deposit_orbit<D, T, FINAL, false>(pc, cur.cell, cur.off, dtdx, T(0), T(1), kc.dt, T(1),
+                                            cur.vb, nodes, nodes_u, J, pg, kc, ms, win_col, ref,
+                                            npieces, st, work, chain, 2);
+        }
+      }
+    } else {
     // the deposits; each round's particle data is loaded one round ahead
     // (slot -1: an empty slot or a failed particle)
     DepIn<T> cur, nxt;
     int kcur = s_dord[wid][lane];
     if (kcur >= 0) dep_load<D, T, S>(cur, pv, c0 + r0 + kcur, kc, rec);
-    T dtdx[3];
-#pragma unroll
-    for (int l = 0; l < 3; l++) dtdx[l] = l < D ? kc.dt * ms.inv_dx[l] : T(0);
 #pragma unroll 1
     for (int q = 0; q < nr; q++) {
       const int knx = q + 1 < nr ? s_dord[wid][(q + 1) * 32 + lane] : -1;
@@ -2021,6 +2064,7 @@ __device__ __forceinline__ void map_chunk_deposit(const PView<S> &pv, const int6
       }
       cur = nxt;
       kcur = knx;
+    }
     }
     __syncwarp();
     for (int e = lane; e < WarpWin<D>::NE; e += 32) {
