@@ -147,7 +147,9 @@ KNOWN_TRAFFIC = {"84faa2124dbc7d66": {"fp64": 139.18e6, "mixed": 71.95e6},
                  # persistent FP64 map; FP32 map as solve + deposit launches (their sum)
                  "61b39d47339a96b4": {"fp64": 145.52e6, "mixed": 116.71e6},
                  # the FP32 solve pass also writes the deposit records
-                 "e739a08bcdd80f01": {"fp64": 145.30e6, "mixed": 118.62e6}}
+                 "e739a08bcdd80f01": {"fp64": 145.30e6, "mixed": 118.62e6},
+                 # two-FMA discrete gradient; deposit records loaded up front
+                 "7624580cdb1973fd": {"fp64": 145.68e6, "mixed": 118.72e6}}
 
 
 def kernel_source_hash():
