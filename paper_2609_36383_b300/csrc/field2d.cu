@@ -19,6 +19,9 @@
 // The transforms are the radix-2 decimation-in-time butterflies of fft.cu
 // (same twiddle tables, same unnormalised convention), so results agree with
 // the generic path to rounding.
+// On a 1D mesh of at most kF1MaxN nodes the same step is one launch of one
+// CTA (k_f1_field): forward transform, CN update, inverse transforms and
+// node records, all in shared memory.
 #include "pic_internal.cuh"
 
 #include <cmath>
@@ -216,6 +219,95 @@ __global__ void k_f2_rows_pack(RowArgs p, T *__restrict__ nodes, T *__restrict__
   }
 }
 
+struct F1Args {
+  const double *jt;                                   // trial current, real (3 comps)
+  const double2 *rho, *phi, *psi, *A, *U;             // accepted state spectra
+  double2 *rho1, *phi1, *psi1, *A1, *U1;              // candidate n+1 spectra
+  double2 *spec;  // final pass: the nc gather fields in real space (times Ng)
+  const double *A_n;                                  // A^n in real space
+  double *A1_real;                                    // A^{n+1} in real space (out)
+  double *Jorb;                                       // cleared
+  const double2 *tw0;
+  int n0, log0, nc, nvp, project, final_pass;
+  double kx_scale, dt, kap2, sigma1, sigma2, inv_ng;
+};
+
+// The 1D field step in one CTA: the mode update is that of k_f2_cols_cn with
+// k = (kx, 0, 0), the records those of k_f2_rows_pack with d = 1.
+template <typename T>
+__global__ void k_f1_field(F1Args p, T *__restrict__ nodes, T *__restrict__ nodes_u) {
+  extern __shared__ double2 sm[];
+  const int n0 = p.n0, Ng = n0, log0 = p.log0;
+  double2 *sj = sm;           // 3 lines of n0
+  double2 *so = sm + 3 * n0;  // nc lines of n0
+  for (int t = threadIdx.x; t < 3 * n0; t += blockDim.x) {
+    const int c = t >> log0, x = t & (n0 - 1);
+    sj[(c << log0) + brev_n(x, log0)] = make_double2(p.jt[(size_t)c * Ng + x], 0.0);
+  }
+  __syncthreads();
+  fft_lines(sj, 3, log0, p.tw0, false);
+  const double2 z = make_double2(0.0, 0.0);
+  const double a = 0.5 * p.dt;
+  for (int x = threadIdx.x; x < n0; x += blockDim.x) {
+    const int xr = brev_n(x, log0);
+    const bool nyq = x == n0 / 2;
+    if (nyq && p.project) {
+      p.rho1[x] = z; p.phi1[x] = z; p.psi1[x] = z;
+      for (int c = 0; c < 3; c++) { p.A1[c * (size_t)Ng + x] = z; p.U1[c * (size_t)Ng + x] = z; }
+      for (int c = 0; c < p.nc; c++) so[c * n0 + xr] = z;
+      continue;
+    }
+    const int ix = x < n0 / 2 ? x : x - n0;
+    const double kx = nyq ? 0.0 : p.kx_scale * ix;
+    const double2 j[3] = {sj[x], sj[n0 + x], sj[2 * n0 + x]};
+    // continuity: rho' = rho - dt (i k . j)
+    const double2 divj = make_double2(-(kx * j[0].y), kx * j[0].x);
+    const double2 rho0 = p.rho[x];
+    const double2 rho1 = make_double2(rho0.x - p.dt * divj.x, rho0.y - p.dt * divj.y);
+    const double2 rhoh = make_double2(0.5 * (rho0.x + rho1.x), 0.5 * (rho0.y + rho1.y));
+    const double b = 0.5 * p.dt * p.kap2 * (kx * kx);
+    double2 phi1, psi1;
+    const double2 phi0 = p.phi[x];
+    const double sr = p.dt * p.kap2 * p.sigma1;
+    cn_pair(a, b, phi0, p.psi[x], make_double2(sr * rhoh.x, sr * rhoh.y), &phi1, &psi1);
+    p.rho1[x] = rho1; p.phi1[x] = phi1; p.psi1[x] = psi1;
+    const double2 phih = make_double2(0.5 * (phi0.x + phi1.x), 0.5 * (phi0.y + phi1.y));
+    so[xr] = c_i(kx, phih);
+    const double sj2 = p.dt * p.kap2 * p.sigma2;
+    for (int c = 0; c < 3; c++) {
+      const double2 A0 = p.A[c * (size_t)Ng + x], U0 = p.U[c * (size_t)Ng + x];
+      double2 A1, U1;
+      cn_pair(a, b, A0, U0, make_double2(sj2 * j[c].x, sj2 * j[c].y), &A1, &U1);
+      p.A1[c * (size_t)Ng + x] = A1;
+      p.U1[c * (size_t)Ng + x] = U1;
+      so[(1 + c) * n0 + xr] = A1;
+      if (p.nc > 4)
+        so[(4 + c) * n0 + xr] = make_double2(0.5 * (U0.x + U1.x), 0.5 * (U0.y + U1.y));
+    }
+  }
+  __syncthreads();
+  fft_lines(so, p.nc, log0, p.tw0, true);
+  for (int g = threadIdx.x; g < n0; g += blockDim.x) {
+    T *rec = nodes + (size_t)g * p.nvp;
+    rec[0] = (T)(so[g].x * p.inv_ng);
+    for (int c = 0; c < 3; c++) {
+      rec[1 + c] = (T)p.A_n[(size_t)c * Ng + g];
+      const double a1 = so[(1 + c) * n0 + g].x * p.inv_ng;
+      rec[4 + c] = (T)a1;
+      p.A1_real[(size_t)c * Ng + g] = a1;
+      p.Jorb[(size_t)c * Ng + g] = 0.0;
+    }
+    for (int c = 7; c < p.nvp; c++) rec[c] = (T)0;
+    if (p.final_pass) {
+      for (int c = 0; c < 3; c++) nodes_u[g * 4 + c] = (T)(so[(4 + c) * n0 + g].x * p.inv_ng);
+      nodes_u[g * 4 + 3] = (T)0;
+      for (int c = 0; c < p.nc; c++) p.spec[(size_t)c * Ng + g] = so[c * n0 + g];
+    }
+  }
+}
+
+constexpr int kF1MaxN = 256;  // one CTA beats the multi-launch path up to here
+
 // largest power of two <= v, at least 1
 int pow2_floor(long long v) {
   int p = 1;
@@ -235,6 +327,37 @@ int field_evaluate(pic_ctx *ctx, const double *jdev, int final_pass) {
   const int n0 = g.n[0], n1 = d > 1 ? g.n[1] : 1;
   const size_t col_smem = sizeof(double2) * (size_t)(3 + nc) * n1;
   const size_t row_smem = sizeof(double2) * (size_t)nc * n0;
+  if (d == 1 && n0 >= 2 && n0 <= kF1MaxN) {
+    F1Args p;
+    p.jt = jdev;
+    p.rho = ctx->rho_h; p.phi = ctx->phi_h; p.psi = ctx->psi_h; p.A = ctx->A_h; p.U = ctx->U_h;
+    p.rho1 = ctx->rho1_h; p.phi1 = ctx->phi1_h; p.psi1 = ctx->psi1_h; p.A1 = ctx->A1_h;
+    p.U1 = ctx->U1_h;
+    p.spec = ctx->work_h;
+    p.A_n = ctx->A_real;
+    p.A1_real = ctx->A1_real;
+    p.Jorb = ctx->Jorb;
+    p.tw0 = ctx->tw[0];
+    p.n0 = n0; p.log0 = g.logn[0]; p.nc = nc; p.nvp = node_record_len(1);
+    p.project = ctx->opt.project_nyquist; p.final_pass = final_pass;
+    p.kx_scale = 2.0 * M_PI / g.L[0];
+    p.dt = ctx->dt;
+    p.kap2 = ctx->opt.kappa * ctx->opt.kappa;
+    p.sigma1 = ctx->opt.sigma1;
+    p.sigma2 = ctx->opt.sigma2;
+    p.inv_ng = 1.0 / Ng;
+    const size_t sm = sizeof(double2) * (size_t)(3 + nc) * n0;  // at most 40 KB
+    int th = nc * n0 / 2;
+    th = th < 64 ? 64 : (th > 256 ? 256 : (th + 31) / 32 * 32);
+    if (ctx->eval_f32)
+      k_f1_field<float><<<1, th, sm, ctx->st>>>(p, ctx->nodes_f, ctx->nodes_u_f);
+    else if (ctx->rsize == 8)
+      k_f1_field<double><<<1, th, sm, ctx->st>>>(p, (double *)ctx->nodes, (double *)ctx->nodes_u);
+    else
+      k_f1_field<float><<<1, th, sm, ctx->st>>>(p, (float *)ctx->nodes, (float *)ctx->nodes_u);
+    KCHECK();
+    return PIC_OK;
+  }
   if (d != 2 || n0 < 2 || n1 < 2 || col_smem > kF2MaxSmem || row_smem > kF2MaxSmem) {
     // the generic path (1D, 3D, very large meshes)
     int e;
