@@ -106,7 +106,10 @@ def test_vjp_is_the_transpose_of_the_jvp(name):
     assert st == 0
     st, H2, jbar = s.eval_map_vjp(j, ybar, 1e-14)
     assert st == 0
-    assert np.abs(H1 - H2).max() <= 1e-12 * np.abs(H1).max()
+    # the two evaluations deposit in different orders: their rounding is
+    # bounded by the gross (one-sign) deposit magnitude, which the
+    # counter-streaming beams' net current can lie far below
+    assert np.abs(H1 - H2).max() <= 1e-12 * max(np.abs(H1).max(), gross)
     lhs, rhs = ybar @ dH, jbar @ dj
     gross_sum = max(np.abs(ybar * dH).sum(), np.abs(jbar * dj).sum())
     print(f"{name}: <ybar, J dj> = {lhs:.12e}, <J^T ybar, dj> = {rhs:.12e}, "
