@@ -83,21 +83,28 @@ __global__ void k_strial(const double *__restrict__ j, const double *__restrict_
 // rt = Ht - jt, and per block: compensated |rt|^2, |Ht|^2, |jt|^2, the
 // largest scaled node residual, and the Gram products of the columns the
 // history would hold if this trial were accepted (ctl->col: ring slots of
-// dR, -1 for the new column rt - r), then of each column with rt.
-__global__ void __launch_bounds__(kST)
-k_sresid(const double *__restrict__ Ht, const double *__restrict__ jt, double *__restrict__ rt,
-         const double *__restrict__ r, const double *__restrict__ dR,
-         const SCtl *__restrict__ ctl, int Ng, double tau_r, double tau_a,
-         double *__restrict__ parts) {
-  __shared__ CSum sh[3][kST / 32];
-  __shared__ double shm[kST / 32];
-  __shared__ double shp[kSMaxPairs][kST / 32];
-  const int ncol = ctl->ncol;
-  int col[kMh + 1];
-  for (int a = 0; a < ncol; a++) col[a] = ctl->col[a];
-  const int npairs = ncol * (ncol + 1) / 2 + ncol;
-  double acc[kSMaxPairs];
-  for (int p = 0; p < npairs; p++) acc[p] = 0.0;
+// dR, -1 for the new column rt - r), then of each column with rt.  The
+// column count NC is a template argument, so that the per-thread products
+// stay in registers; kSR-thread blocks, one node per thread.
+constexpr int kSR = 128;
+
+template <int NC>
+__device__ __forceinline__ void sresid_pass(const double *__restrict__ Ht,
+                                            const double *__restrict__ jt,
+                                            double *__restrict__ rt,
+                                            const double *__restrict__ r,
+                                            const double *__restrict__ dR,
+                                            const SCtl *__restrict__ ctl, int Ng, double tau_r,
+                                            double tau_a, double *__restrict__ parts,
+                                            CSum (*sh)[kSR / 32], double *shm,
+                                            double (*shp)[kSR / 32]) {
+  constexpr int NP = NC * (NC + 1) / 2 + NC;
+  int col[NC > 0 ? NC : 1];
+#pragma unroll
+  for (int a = 0; a < NC; a++) col[a] = ctl->col[a];
+  double acc[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int p = 0; p < NP; p++) acc[p] = 0.0;
   CSum cs[3] = {csum_zero(), csum_zero(), csum_zero()};
   double mx = 0.0;
   const size_t N3 = 3 * (size_t)Ng;
@@ -112,14 +119,18 @@ k_sresid(const double *__restrict__ Ht, const double *__restrict__ jt, double *_
       rr += rv * rv;
       hh += hv * hv;
       jj += jv * jv;
-      if (ncol > 0) {
-        double v[kMh + 1];
-        for (int a = 0; a < ncol; a++)
+      if (NC > 0) {
+        double v[NC > 0 ? NC : 1];
+#pragma unroll
+        for (int a = 0; a < NC; a++)
           v[a] = col[a] < 0 ? rv - r[i] : dR[(size_t)col[a] * N3 + i];
         int p = 0;
-        for (int a = 0; a < ncol; a++)
-          for (int b = a; b < ncol; b++) acc[p++] += v[a] * v[b];
-        for (int a = 0; a < ncol; a++) acc[p++] += v[a] * rv;
+#pragma unroll
+        for (int a = 0; a < NC; a++)
+#pragma unroll
+          for (int b = a; b < NC; b++) acc[p++] += v[a] * v[b];
+#pragma unroll
+        for (int a = 0; a < NC; a++) acc[p++] += v[a] * rv;
       }
     }
     csum_add(cs[0], rr);
@@ -134,7 +145,8 @@ k_sresid(const double *__restrict__ Ht, const double *__restrict__ jt, double *_
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
   if (lane == 0) shm[wid] = mx;
-  for (int p = 0; p < npairs; p++) {
+#pragma unroll
+  for (int p = 0; p < NP; p++) {
     double x = acc[p];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if (lane == 0) shp[p][wid] = x;
@@ -143,19 +155,49 @@ k_sresid(const double *__restrict__ Ht, const double *__restrict__ jt, double *_
   double *out = parts + (size_t)blockIdx.x * kSStride;
   if (threadIdx.x < 3) {
     CSum t = csum_zero();
-    for (int w = 0; w < kST / 32; w++) t = csum_merge(t, sh[threadIdx.x][w]);
+    for (int w = 0; w < kSR / 32; w++) t = csum_merge(t, sh[threadIdx.x][w]);
     out[2 * threadIdx.x] = t.s;
     out[2 * threadIdx.x + 1] = t.c;
   } else if (threadIdx.x == 3) {
     double m = 0.0;
-    for (int w = 0; w < kST / 32; w++) m = fmax(m, shm[w]);
+    for (int w = 0; w < kSR / 32; w++) m = fmax(m, shm[w]);
     out[6] = m;
-  } else if (threadIdx.x >= 32 && threadIdx.x < 32 + npairs) {
+  } else if (threadIdx.x >= 32 && threadIdx.x < 32 + NP) {
     const int p = threadIdx.x - 32;
     double t = 0.0;
-    for (int w = 0; w < kST / 32; w++) t += shp[p][w];
+    for (int w = 0; w < kSR / 32; w++) t += shp[p][w];
     out[8 + p] = t;
   }
+}
+
+__global__ void __launch_bounds__(kSR)
+k_sresid(const double *__restrict__ Ht, const double *__restrict__ jt, double *__restrict__ rt,
+         const double *__restrict__ r, const double *__restrict__ dR,
+         const SCtl *__restrict__ ctl, int Ng, double tau_r, double tau_a,
+         double *__restrict__ parts) {
+  __shared__ CSum sh[3][kSR / 32];
+  __shared__ double shm[kSR / 32];
+  __shared__ double shp[kSMaxPairs][kSR / 32];
+  static_assert(kMh + 1 == 9, "one case per Gram column count below");
+  static_assert(32 + kSMaxPairs <= kSR, "a thread per Gram product in the block merge");
+#define PIC_SRESID(NC)                                                                     \
+  case NC:                                                                                 \
+    sresid_pass<NC>(Ht, jt, rt, r, dR, ctl, Ng, tau_r, tau_a, parts, sh, shm, shp); \
+    break;
+  switch (ctl->ncol) {  // the same for every thread
+    PIC_SRESID(0)
+    PIC_SRESID(1)
+    PIC_SRESID(2)
+    PIC_SRESID(3)
+    PIC_SRESID(4)
+    PIC_SRESID(5)
+    PIC_SRESID(6)
+    PIC_SRESID(7)
+    PIC_SRESID(8)
+    PIC_SRESID(9)
+    default: break;
+  }
+#undef PIC_SRESID
 }
 
 __device__ bool sdev_solve(int m, double *A, double *b) {
@@ -444,7 +486,7 @@ int sgrid(size_t n) {
 }
 
 int sresid_blocks(const pic_ctx *ctx) {
-  size_t b = ((size_t)ctx->g.Ng + kST - 1) / kST;
+  size_t b = ((size_t)ctx->g.Ng + kSR - 1) / kSR;
   if (b > (size_t)kSMaxBlocks) b = kSMaxBlocks;
   return (int)(b < 1 ? 1 : b);
 }
@@ -481,7 +523,7 @@ int enqueue_round(pic_ctx *ctx, const StepConst &sc, double tr, double ta, int f
   if ((e = particles_map_launch(ctx, sc, final_pass))) return e;
   if ((e = field_project_real(ctx, ctx->Jorb, ctx->Ht, 3))) return e;
   const int nb = sresid_blocks(ctx);
-  k_sresid<<<nb, kST, 0, ctx->st>>>(ctx->Ht, ctx->jt, ctx->rt, ctx->r, ctx->dR, ctx->sctl,
+  k_sresid<<<nb, kSR, 0, ctx->st>>>(ctx->Ht, ctx->jt, ctx->rt, ctx->r, ctx->dR, ctx->sctl,
                                      ctx->g.Ng, tr, ta, ctx->sred);
   KCHECK();
   k_sctl<<<1, kST, 0, ctx->st>>>(ctx->sctl, ctx->sred, nb, ctx->cnt_dev, ctx->map_timer,
