@@ -140,7 +140,7 @@ def algorithmic_bytes(dim, rsize, pushes):
 
 
 # DRAM bytes per launch of the particle-map kernels (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of two launches) from ncu captures of the kernel
+# dram__bytes_write.sum, mean over the captured launches) from ncu captures of the kernel
 # sources whose hash (kernel_source_hash) is the key (profiles/k_map_traffic_*.md);
 # the roofline reports null traffic once those sources have changed since.
 KNOWN_TRAFFIC = {"84faa2124dbc7d66": {"fp64": 139.18e6, "mixed": 71.95e6},
